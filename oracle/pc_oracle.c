@@ -85,10 +85,16 @@ typedef struct {
 /* ------------------------------------------------------------------ */
 /* Chebyshev-Gauss-Lobatto nodes, Eq. (chnodes2) with n = N + 1 nodes:  */
 /* tau_j = -cos(j pi / N), j = 0..N, so tau_0 = -1 is the segment start.*/
+/* Evaluated as sin(pi (2j - N) / (2N)), the same value, so that the    */
+/* nodes are exactly antisymmetric and the middle node is exactly 0.    */
 /* ------------------------------------------------------------------ */
-void ora_cgl_nodes(int N, double *tau) {
+static long double ora_tau_ld(int j, int N) {
   const long double pi = 3.141592653589793238462643383279502884L;
-  for (int j = 0; j <= N; j++) tau[j] = (double)(-cosl(pi * (long double)j / (long double)N));
+  return sinl(pi * (long double)(2 * j - N) / (long double)(2 * N));
+}
+
+void ora_cgl_nodes(int N, double *tau) {
+  for (int j = 0; j <= N; j++) tau[j] = (double)ora_tau_ld(j, N);
 }
 
 /* ------------------------------------------------------------------ */
@@ -107,7 +113,6 @@ void ora_cgl_nodes(int N, double *tau) {
 /* truncated = 1 drops beta_{N+1} (the paper's B has only N+1 rows).     */
 /* ------------------------------------------------------------------ */
 void ora_pc_operator(int N, int truncated, double *K) {
-  const long double pi = 3.141592653589793238462643383279502884L;
   const int n = N + 1;
   const int nb = N + 2; /* beta_0 .. beta_{N+1} */
   long double *T = (long double *)malloc(sizeof(long double) * (size_t)(N + 2) * n);   /* T[k][j] */
@@ -115,7 +120,7 @@ void ora_pc_operator(int N, int truncated, double *K) {
   long double *Int = (long double *)calloc((size_t)nb * n, sizeof(long double));       /* beta = Int a */
   long double *IF = (long double *)calloc((size_t)nb * n, sizeof(long double));        /* Int * Fit */
   long double *tau = (long double *)malloc(sizeof(long double) * n);
-  for (int j = 0; j < n; j++) tau[j] = -cosl(pi * (long double)j / (long double)N);
+  for (int j = 0; j < n; j++) tau[j] = ora_tau_ld(j, N);
   /* T_k(tau_j) by the three-term recurrence, k = 0..N+1 */
   for (int j = 0; j < n; j++) {
     T[0 * n + j] = 1.0L;
