@@ -1,0 +1,351 @@
+"""Benchmark: trajectories/s of the batched Picard-Chebyshev propagator on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pc_propagate call over the whole workload: 4096 trajectories
+of the Sun + 8 planets + Moon system, each starting 0.5-1.5 days before a close
+Venus flyby (periapsis 1e4-5e4 km), propagated for 4 years at Chebyshev degree
+128, tol 1e-13 (seeded synthetic stand-in for the paper's 13,509-trajectory
+data set).  Every step runs the whole hot path on the GPU: per-trajectory
+segment schedule, ephemeris at the nodes, Keplerian warm start, force,
+operator contraction, convergence tests, stitching.
+
+value: trajectories/s with inputs resident in HBM (CUDA events on the launch
+stream, L2 flushed between steps).  e2e: the same through the C ABI with the
+initial states copied from pinned host memory and the final states + status
+copied back inside the timed region.  --impl reference times the CPU oracle
+on a bounded sample of the same workload on the host cores.
+
+With N > 1 (torchrun) each rank propagates its own 4096 trajectories (weak
+scaling, no data-path collective); rank 0 prints the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trajectories/s (N-body, <=1e-10 rel err): mixed+batched vs plain FP64 GPU"
+UNIT = "trajectories/s"
+IC_PER_RANK = 4096
+
+# Per-launch DRAM bytes (read + write) of the dominant kernel from an ncu
+# capture of the same kernel and workload (profiles/contract_cfg2_ncu.txt);
+# None until a capture of the current kernel exists.
+TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp64_tensor_peak_tflops():
+    """FP64 tensor-core peak: the measured bf16 dense peak times the nominal
+    FP64/bf16 ratio (1.25 / 2250 TFLOP/s); fallback 1.9 PFLOP/s bf16."""
+    pk = _peaks()
+    bf16 = pk.get("bf16_tflops")
+    src = "measured bf16 x nominal fp64/bf16 ratio"
+    if bf16 is None:
+        bf16, src = 1900.0, "fallback bf16 x nominal fp64/bf16 ratio"
+    return bf16 * 1.25 / 2250.0, src
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int = 0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thr = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thr = threading.Thread(target=self._read, daemon=True)
+        self.thr.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thr:
+            self.thr.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(n_total: int, world: int, rank: int):
+    """Contiguous slice of the trajectory index space owned by `rank`."""
+    lo = n_total * rank // world
+    hi = n_total * (rank + 1) // world
+    return lo, hi
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_rate(w, n_sample: int, threads: int):
+    """Times the CPU oracle on the first n_sample trajectories; returns (traj/s, seconds)."""
+    from oracle import oracle as ora
+    ora.build()
+    m = ora.Model.from_workload(w)
+    o = ora.Opts(N=w.N, segments=w.segments, seg_mode=w.seg_mode, tol=w.tol, max_iters=w.max_iters,
+                 max_depth=w.max_depth)
+    x = w.x0[:n_sample]
+    t = time.perf_counter()
+    ora.propagate(m, o, x, w.t0, w.tf, threads=threads)
+    dt = time.perf_counter() - t
+    return n_sample / dt, dt
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the oracle as it stands on the host cores."""
+    if rank != 0:
+        return 0
+    from paper_2301_03989_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    w = W.config2(M=IC_PER_RANK)
+    n_sample = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_rate(w, max(cores, n_sample // 4), cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(w, n_sample, cores)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = n_sample / (ms / 1000.0)
+    sample = f"first {n_sample} of {w.n_ic} trajectories of the workload per step, full 4-year arcs"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_ic": n_sample, "N": w.N, "arc_years": 4,
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def contract_flops_per_sweep(N: int) -> float:
+    """Useful FP64 flops of one trajectory-sweep of the contraction: rows 1..N
+    of K (row 0 is zero) times N+1 nodes times 6 components, 2 flops each."""
+    return 2.0 * N * (N + 1) * 6
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2301_03989_gb300 import build as B
+    from paper_2301_03989_gb300 import pcprop as pc
+    from paper_2301_03989_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.build()
+    wall = W.config2(M=IC_PER_RANK * world)
+    lo, hi = shard(wall.n_ic, world, rank)
+    w = wall.subset(np.arange(lo, hi))
+    M = w.n_ic
+    plan = pc.plan_from_workload(w)
+    stream = torch.cuda.Stream(device=dev)
+    x0 = torch.as_tensor(W.to_planar(w.x0), device=dev)
+    xf = torch.zeros_like(x0)
+    st = torch.zeros(M, dtype=torch.int32, device=dev)
+    it = torch.zeros(M, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def step():
+        code, rounds = pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, iters=it, stream=stream)
+        return rounds
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        pc.set_profiling(plan, True)
+        pc.kernel_times(plan)                       # clear
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        rounds_total = 0
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            rounds_total += step()
+            ev1[k].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        ktimes = pc.kernel_times(plan)
+        pc.set_profiling(plan, False)
+        iters = it.cpu().numpy().astype(np.int64)
+        status = st.cpu().numpy()
+
+        # end to end through the C ABI with host buffers
+        hx0 = torch.as_tensor(W.to_planar(w.x0)).pin_memory()
+        hxf = torch.empty_like(hx0).pin_memory()
+        hst = torch.empty(M, dtype=torch.int32).pin_memory()
+        e2e_ms = []
+        for k in range(max(1, args.steps)):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            x0.copy_(hx0, non_blocking=True)
+            step()
+            hxf.copy_(xf, non_blocking=True)
+            hst.copy_(st, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = max_over_ranks(ms, world, dev)
+    e2e = sum(e2e_ms) / len(e2e_ms)
+    e2e_max = max_over_ranks(e2e, world, dev)
+    total_ic = wall.n_ic
+    value = total_ic / (ms_max / 1000.0)
+    e2e_value = total_ic / (e2e_max / 1000.0)
+
+    # roofline of the dominant kernel (the FP64 tensor-core contraction)
+    kname = max(ktimes, key=lambda k: ktimes[k][1])
+    launches_c, ms_c = ktimes["contract"]
+    sweeps = int(iters.sum()) * args.steps                 # trajectory-sweeps over the timed steps
+    flops = contract_flops_per_sweep(w.N) * sweeps
+    achieved = flops / (ms_c / 1000.0) / 1e12 if ms_c > 0 else 0.0
+    peak, peak_src = fp64_tensor_peak_tflops()
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+            "kernel": "k_contract (FP64 DMMA m16n8k4)", "dtype": "f64", "peak_source": peak_src,
+            "launches": launches_c, "avg_launch_us": 1000.0 * ms_c / max(1, launches_c),
+            "algorithmic_flops_per_launch": flops / max(1, launches_c),
+            "kernel_share": {k: v[1] / max(1e-9, sum(x[1] for x in ktimes.values())) for k, v in ktimes.items()},
+            "dominant_by_time": kname}
+
+    line = None
+    if rank == 0:
+        cores = os.cpu_count() or 1
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, secs = oracle_rate(w, min(M, args.cpu_sample), cores)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"first {min(M, args.cpu_sample)} trajectories of the workload, full 4-year arcs, "
+                             f"{secs:.1f} s on {cores} threads"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_ic_per_gpu": M, "N": w.N, "arc_years": 4, "tol": w.tol,
+                       "path": "plain FP64 batched sweep (per-trajectory segments, DMMA contraction)",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx0.numel() * 8),
+                    "d2h_bytes_per_step": int(hxf.numel() * 8 + hst.numel() * 4)},
+            "gpu_launches": int(sum(v[0] for v in ktimes.values()) + 2 * args.steps),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "stats": {"sweep_rounds_per_step": rounds_total / max(1, args.steps),
+                      "trajectory_sweeps_per_step": int(iters.sum()),
+                      "status_nonzero": int((status != 0).sum()),
+                      "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()}},
+        }
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--ref-sample", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * pc.h -- C ABI of the GB300 (sm_103a) batched Picard-Chebyshev propagator.
+ *
+ * Method: augmented Picard-Chebyshev (PC) integration of Masat, Colombo &
+ * Boutonnet, "GPU-based high-precision orbital propagation of large sets of
+ * initial conditions through Picard-Chebyshev augmentation" (arXiv
+ * 2301.03989).  Many non-interacting, massless trajectories are propagated at
+ * once under the Newtonian gravity of a central body and B perturbing bodies
+ * whose positions come from a Chebyshev ephemeris table.  Each trajectory is
+ * split into segments; on each segment the Picard iteration (Eq. 2) is run in
+ * the matrix form of Section "Matrix form for vectorized and parallel
+ * computation" until the sweep-to-sweep change drops below a tolerance.  The
+ * trajectories are stacked column-wise (Section "One-level augmentation") in
+ * the component-planar layout of Section "Dynamics model, array sorting, and
+ * CUDA kernel".
+ *
+ * Units: km, s, km^3/s^2.  All floating-point arguments are IEEE FP64.
+ *
+ * Layouts: a batch of M states is "planar": x[c * M + m] for component c in
+ * 0..5 = (x, y, z, vx, vy, vz) and trajectory m -- component-stacked columns
+ * as in the paper.
+ *
+ * Ownership: the caller owns every buffer it passes (device or host, as each
+ * argument states).  The plan owns its operator, its copy of the force model
+ * and ephemeris, and its device workspace.
+ *
+ * Errors: every entry point returns a pc_status; nothing aborts, prints or
+ * traps.  Per-trajectory outcomes go to the optional status[] array.
+ *
+ * Streams: work is issued on the CUDA stream passed in (NULL = legacy default
+ * stream).  Use one plan per concurrently used stream: a plan's workspace is
+ * shared by all its calls.
+ */
+#ifndef PC_H_
+#define PC_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pc_plan pc_plan; /* opaque, owned by the library */
+
+typedef enum {
+  PC_OK = 0,          /* success */
+  PC_EINVAL = 1,      /* bad argument (sizes, NULL pointers, options, arc outside the table) */
+  PC_ENOMEM = 2,      /* device or host allocation failed */
+  PC_ECUDA = 3,       /* a CUDA runtime call failed */
+  PC_ENOTCONV = 4,    /* finished, but at least one trajectory stopped early (status bit 4 or 8) */
+  PC_ENONFINITE = 5   /* reserved: a non-finite value where a finite one is required */
+} pc_status;
+
+/* Per-trajectory status bits written to status[] (0 = converged everywhere). */
+#define PC_IC_STALLED 1        /* a segment was accepted by the stall rule (change stopped falling near tol) */
+#define PC_IC_UNRESOLVED 2     /* a segment at the deepest halving still failed the resolution test */
+#define PC_IC_NOT_CONVERGED 4  /* stopped: a segment did not converge even at the deepest halving */
+#define PC_IC_NONFINITE 8      /* stopped: non-finite input, or the iteration blew up at the deepest halving */
+
+/* Force model: a(r, t) = -mu_c r/|r|^3 - sum_b mu_b [(r - r_b)/|r - r_b|^3 + r_b/|r_b|^3]
+ * (heliocentric Newtonian point masses; the bracket's second term, the
+ * indirect term, only when `indirect` != 0).  The paper's own force is the
+ * relativistic EIH model (Section "Dynamics model"); this library evaluates
+ * the Newtonian one. */
+typedef struct {
+  int n_bodies;        /* B >= 0 perturbing bodies */
+  double mu_central;   /* GM of the central body, > 0 */
+  const double *mu;    /* host [n_bodies], copied at plan creation */
+  int indirect;        /* 1: include the indirect term */
+} pc_force_model;
+
+/* Ephemeris: granule g covers [t_begin + g*granule_s, t_begin + (g+1)*granule_s)
+ * (a time on a boundary uses the later granule; times outside the table use
+ * the nearest granule); inside it sigma = 2 (t - t_g)/granule_s - 1 and
+ * r_b(t) = sum_k coef[b][g][axis][k] T_k(sigma).  The paper evaluates the
+ * planetary data once per set of node times, before the iterations (Section
+ * "Dynamics model"); so does this library, once per segment. */
+typedef struct {
+  int n_bodies;         /* must equal the force model's */
+  double t_begin;       /* s */
+  double granule_s;     /* > 0 */
+  int degree;           /* >= 0 */
+  int n_granules;       /* >= 1 */
+  const double *coef;   /* host [n_bodies][n_granules][3][degree+1], copied at plan creation */
+} pc_ephemeris;
+
+#define PC_PREC_FP64 0   /* every sweep in FP64 */
+#define PC_PREC_MIXED 1  /* FP32 sweeps on the deviation from the warm start until the change is below
+                            switch_tol, then FP64 sweeps to tol (not in the paper: an extension) */
+
+typedef struct {
+  double tol;          /* stopping tolerance on the sweep-to-sweep change (overridden per call) */
+  int relative;        /* 1: change relative to |r| and |v| of the new iterate; 0: absolute */
+  int max_iters;       /* sweeps per segment attempt (>= 1) */
+  int max_depth;       /* times a segment may be halved, 0..30 */
+  int warm_start;      /* 1: Keplerian two-body guess (central body only); 0: all nodes = x0 */
+  int seg_mode;        /* 0: `segments` equal segments per arc; 1: per osculating period of x0 */
+  int truncated;       /* 1: drop the degree-(N+1) term of the integral (the paper's N+1-row B) */
+  int stall_sweeps;    /* accept a segment when the change has not improved for this many sweeps ... */
+  double stall_factor; /* ... and the best change is below stall_factor * tol */
+  double div_limit;    /* a change above this, or non-finite, fails the attempt */
+  double trunc_tol;    /* resolution test on the Chebyshev tail of the force fit (<= 0 disables) */
+  int precision;       /* PC_PREC_FP64 or PC_PREC_MIXED */
+  double switch_tol;   /* mixed precision: FP32 sweeps until the change is below this */
+  long long max_rounds;/* safety cap on sweep rounds per call (0 = 10,000,000) */
+} pc_options;
+
+/* Fills *o with the defaults: tol 1e-13, relative 1, max_iters 60, max_depth 8,
+ * warm_start 1, seg_mode 0, truncated 0, stall_sweeps 5, stall_factor 1e3,
+ * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 1e-6, max_rounds 0.
+ * Returns PC_EINVAL if o is NULL. */
+pc_status pc_options_default(pc_options *o);
+
+/* Creates a plan for degree-N segments (N + 1 Chebyshev-Gauss-Lobatto nodes,
+ * Eq. chnodes1/2 with tau_0 = -1 at the segment start), `segments` base
+ * segments (per arc, or per osculating period with seg_mode 1; Section
+ * "Matrix form", piecewise integration).  Builds the PC operator K (the
+ * paper's C [S A; A], Eq. for B and y = C B) in extended precision, uploads
+ * it with the force model and ephemeris to the current CUDA device.
+ * N in [2, 512]; segments >= 1; opt may be NULL (defaults).
+ * Errors: PC_EINVAL, PC_ENOMEM, PC_ECUDA.  *out is NULL on failure. */
+pc_status pc_plan_create(int N, int segments, const pc_force_model *force, const pc_ephemeris *ephem,
+                         const pc_options *opt, pc_plan **out);
+
+/* Propagates n_ic trajectories from t0 to tf (tf < t0 integrates backward).
+ *   x0      device, planar [6][n_ic], read only
+ *   tol     stopping tolerance for this call (<= 0: the plan's)
+ *   xf      device, planar [6][n_ic], written: state at tf, or at the last
+ *           accepted segment boundary of a trajectory that stopped early
+ *   status  device [n_ic] PC_IC_* bits, or NULL
+ *   iters   device [n_ic] sweeps spent (all attempts), or NULL
+ *   stream  cudaStream_t or NULL
+ * Each trajectory runs its own segment schedule (equal base segments, halved
+ * on failure, grown back after success) so trajectories never wait on each
+ * other.  Work is queued on `stream`; the call returns once every trajectory
+ * has finished (it polls a device counter).  The arc must lie inside the
+ * ephemeris table when n_bodies > 0.  n_ic = 0 is a no-op.
+ * Returns PC_OK, PC_ENOTCONV (some trajectory stopped early), PC_EINVAL,
+ * PC_ENOMEM or PC_ECUDA. */
+pc_status pc_propagate(pc_plan *plan, long long n_ic, const double *x0, double t0, double tf, double tol,
+                       double *xf, int *status, int *iters, void *stream);
+
+/* Same as pc_propagate, with optional extra outputs (NULL = not wanted):
+ *   nseg    device [n_ic]: accepted segments
+ *   ckpt    device [n_ic][max_ckpt][7]: (t_a, x(t_a)) at the start of each of the
+ *           first max_ckpt accepted segments -- the segment-boundary checkpoints
+ *   rounds  host: number of sweep rounds the call ran */
+pc_status pc_propagate_ex(pc_plan *plan, long long n_ic, const double *x0, double t0, double tf, double tol,
+                          double *xf, int *status, int *iters, int *nseg, int max_ckpt, double *ckpt,
+                          long long *rounds, void *stream);
+
+/* ---- Kernel-level entry points -------------------------------------------
+ * Each runs one of the device kernels the sweep uses, on caller buffers, so a
+ * step can be checked on its own.  All pointers are device pointers; the calls
+ * are asynchronous on `stream` and use the plan's workspace (same rule as
+ * pc_propagate: one plan per concurrently used stream). */
+
+/* Ephemeris (Clenshaw) at n_pts times t [n_pts]: rb planar [n_bodies][3][n_pts]. */
+pc_status pc_eval_ephemeris(pc_plan *plan, long long n_pts, const double *t, double *rb, void *stream);
+
+/* Dynamics f(y, t) = (v, a(r, t)) of Eq. (ibvp) with the plan's force model at
+ * n_pts states y (planar [6][n_pts]) and times t [n_pts]: f planar [6][n_pts]. */
+pc_status pc_eval_dynamics(pc_plan *plan, long long n_pts, const double *t, const double *y, double *f,
+                           void *stream);
+
+/* Keplerian warm start (central body only): x = two-body propagation of x0 by
+ * dt, planar [6][n_pts]; states that are not bound ellipses are copied
+ * unchanged (the cold start). */
+pc_status pc_eval_warm_start(pc_plan *plan, long long n_pts, const double *x0, const double *dt, double *x,
+                             void *stream);
+
+/* The operator contraction of one sweep, y_j = x0 + sum_k K_jk g_k (the
+ * paper's B = [S A F + 2 y0; A F], y = C B with F = omega2 f already scaled),
+ * for n_ic trajectories: x0 planar [6][n_ic]; g and y node-major planar
+ * [N+1][6][n_ic]. */
+pc_status pc_apply_operator(pc_plan *plan, long long n_ic, const double *x0, const double *g, double *y,
+                            void *stream);
+
+/* ---- Per-kernel timing ----------------------------------------------------
+ * With profiling on, pc_propagate / pc_propagate_ex record a CUDA event
+ * between consecutive kernels of every sweep round on the call's stream; the
+ * elapsed times are summed when pc_plan_kernel_times is called (not during the
+ * propagation, so the host adds no gap to the timed work). */
+#define PC_KERNEL_SETUP 0     /* new segments: node times, ephemeris, warm start */
+#define PC_KERNEL_FORCE 1     /* F = omega2 f(Y, t) */
+#define PC_KERNEL_CONTRACT 2  /* Y' = x0 + K F and the per-trajectory change */
+#define PC_KERNEL_CONTROL 3   /* stop tests, segment accept / halve / advance */
+#define PC_KERNEL_KINDS 4
+typedef struct {
+  long long launches[PC_KERNEL_KINDS];
+  double ms[PC_KERNEL_KINDS]; /* summed device time */
+} pc_kernel_times;
+
+/* on != 0 turns per-kernel event recording on for later calls. */
+pc_status pc_plan_set_profiling(pc_plan *plan, int on);
+
+/* Sums the recorded intervals into *out (after synchronizing the recorded
+ * events) and clears them. */
+pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
+
+/* Copies the plan's operator K ((N+1) x (N+1), row-major) and nodes tau (N+1)
+ * to host buffers (either may be NULL).  For tests and diagnostics. */
+pc_status pc_plan_operator(const pc_plan *plan, double *K, double *tau);
+
+/* Frees the plan (NULL is allowed).  Must not race with a call using it. */
+void pc_plan_destroy(pc_plan *plan);
+
+/* Static English description of a status code. */
+const char *pc_status_string(pc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC_H_ */

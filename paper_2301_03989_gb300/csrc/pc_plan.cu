@@ -1,0 +1,269 @@
+// Plan creation: operator construction (host, extended precision), model
+// upload, workspace management, status strings.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pc_internal.h"
+
+using namespace pcx;
+
+namespace {
+
+// T_m(tau_j) on the CGL nodes tau_j = -cos(j pi/N): with theta_j = pi - j pi/N,
+// T_m(tau_j) = cos(m theta_j) = (-1)^m cos(m j pi / N).  The angle m*j is
+// reduced modulo 2N in integers before the cosine, so every entry is the
+// correctly reduced extended-precision value.
+long double cheb_at_node(int m, int j, int N) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  long long q = ((long long)m * (long long)j) % (2LL * N);
+  long double c = cosl(pi * (long double)q / (long double)N);
+  return (m & 1) ? -c : c;
+}
+
+// The PC operator, built column by column.  Column k is the map from a unit
+// force at node k to the state increments: the Lagrange basis polynomial l_k
+// on the CGL nodes has Chebyshev coefficients
+//   a_m = (2/N) * T_m(tau_k) / (c_k c_m),   c_0 = c_N = 2, otherwise 1,
+// its integral from -1 has coefficients b_1 = a_0 - a_2/2,
+// b_m = (a_{m-1} - a_{m+1})/(2m) (m >= 2, a_{N+1} = a_{N+2} = 0) and b_0 fixed
+// by the integral vanishing at tau = -1, and K[j][k] = sum_m b_m T_m(tau_j).
+// This is the paper's chain of matrix products (A, S, C) collapsed into one
+// (N+1) x (N+1) matrix acting on omega2-scaled forces.
+void build_operator(int N, int truncated, double *K /* (N+1)^2 */) {
+  const int n = N + 1;
+  std::vector<long double> a(N + 3), b(N + 2);
+  std::vector<long double> T((size_t)(N + 2) * n);
+  for (int m = 0; m <= N + 1; m++)
+    for (int j = 0; j < n; j++) T[(size_t)m * n + j] = cheb_at_node(m, j, N);
+  for (int k = 0; k < n; k++) {
+    const long double ck = (k == 0 || k == N) ? 2.0L : 1.0L;
+    for (int m = 0; m <= N + 2; m++) a[m] = 0.0L;
+    for (int m = 0; m <= N; m++) {
+      const long double cm = (m == 0 || m == N) ? 2.0L : 1.0L;
+      a[m] = 2.0L / (long double)N * T[(size_t)m * n + k] / (ck * cm);
+    }
+    b[1] = a[0] - 0.5L * a[2];
+    for (int m = 2; m <= N + 1; m++) b[m] = (a[m - 1] - a[m + 1]) / (2.0L * (long double)m);
+    if (truncated) b[N + 1] = 0.0L;
+    long double s = 0.0L;
+    for (int m = 1; m <= N + 1; m++) s += (m & 1) ? -b[m] : b[m];  // value at tau = -1
+    b[0] = -s;
+    for (int j = 0; j < n; j++) {
+      long double y = 0.0L;
+      for (int m = 0; m <= N + 1; m++) y += b[m] * T[(size_t)m * n + j];
+      K[(size_t)j * n + k] = (double)y;
+    }
+  }
+  for (int k = 0; k < n; k++) K[k] = 0.0;  // node 0 is the initial condition itself
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+}
+
+}  // namespace
+
+extern "C" pc_status pc_options_default(pc_options *o) {
+  if (!o) return PC_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-13;
+  o->relative = 1;
+  o->max_iters = 60;
+  o->max_depth = 8;
+  o->warm_start = 1;
+  o->seg_mode = 0;
+  o->truncated = 0;
+  o->stall_sweeps = 5;
+  o->stall_factor = 1e3;
+  o->div_limit = 1e3;
+  o->trunc_tol = 1e-13;
+  o->precision = PC_PREC_FP64;
+  o->switch_tol = 1e-6;
+  o->max_rounds = 0;
+  return PC_OK;
+}
+
+static pc_status check_options(const pc_options &o) {
+  if (!(o.tol >= 0.0) || o.max_iters < 1 || o.max_depth < 0 || o.max_depth > 30 || o.stall_sweeps < 1 ||
+      !(o.stall_factor >= 0.0) || !(o.div_limit > 0.0) || (o.seg_mode != 0 && o.seg_mode != 1) ||
+      (o.precision != PC_PREC_FP64 && o.precision != PC_PREC_MIXED) || o.max_rounds < 0)
+    return PC_EINVAL;
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *force, const pc_ephemeris *ephem,
+                                    const pc_options *opt, pc_plan **out) {
+  if (!out) return PC_EINVAL;
+  *out = nullptr;
+  if (N < 2 || N > kMaxN || segments < 1 || !force) return PC_EINVAL;
+  const int B = force->n_bodies;
+  if (B < 0 || B > kMaxBodies || !(force->mu_central > 0.0) || (B > 0 && !force->mu)) return PC_EINVAL;
+  if (B > 0) {
+    if (!ephem || ephem->n_bodies != B || !(ephem->granule_s > 0.0) || ephem->degree < 0 ||
+        ephem->n_granules < 1 || !ephem->coef)
+      return PC_EINVAL;
+  }
+  pc_options o;
+  pc_options_default(&o);
+  if (opt) o = *opt;
+  if (check_options(o) != PC_OK) return PC_EINVAL;
+
+  pc_plan *p = new (std::nothrow) pc_plan();
+  if (!p) return PC_ENOMEM;
+  p->N = N;
+  p->n = N + 1;
+  p->kpad = (p->n + 3) / 4 * 4;
+  p->rows_pad = (N + 15) / 16 * 16;
+  p->segments = segments;
+  p->opt = o;
+  cudaGetDevice(&p->device);
+
+  const int n = p->n;
+  p->h_K = (double *)std::malloc(sizeof(double) * n * n);
+  p->h_tau = (double *)std::malloc(sizeof(double) * n);
+  if (!p->h_K || !p->h_tau) { pc_plan_destroy(p); return PC_ENOMEM; }
+  build_operator(N, o.truncated, p->h_K);
+  // tau_j = -cos(j pi/N) written as sin(pi (2j - N)/(2N)): exactly antisymmetric, 0 in the middle
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int j = 0; j < n; j++) p->h_tau[j] = (double)sinl(pi * (long double)(2 * j - N) / (long double)(2 * N));
+
+  // Device operator: rows = nodes 1..N, zero-padded to rows_pad x kpad.
+  std::vector<double> Kd((size_t)p->rows_pad * p->kpad, 0.0);
+  for (int r = 0; r < N; r++)
+    for (int k = 0; k < n; k++) Kd[(size_t)r * p->kpad + k] = p->h_K[(size_t)(r + 1) * n + k];
+  cudaError_t e = dalloc(&p->d_K, Kd.size());
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_K, Kd.data(), sizeof(double) * Kd.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dalloc(&p->d_tau, n);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_tau, p->h_tau, sizeof(double) * n, cudaMemcpyHostToDevice);
+  Model &m = p->model;
+  m.B = B;
+  m.mu_c = force->mu_central;
+  m.indirect = force->indirect ? 1 : 0;
+  if (B > 0) {
+    m.t_begin = ephem->t_begin;
+    m.granule = ephem->granule_s;
+    m.deg = ephem->degree;
+    m.n_gr = ephem->n_granules;
+    size_t nc = (size_t)B * ephem->n_granules * 3 * (ephem->degree + 1);
+    if (e == cudaSuccess) e = dalloc(&p->d_mu, B);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_mu, force->mu, sizeof(double) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dalloc(&p->d_coef, nc);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_coef, ephem->coef, sizeof(double) * nc, cudaMemcpyHostToDevice);
+  } else {
+    m.t_begin = 0.0;
+    m.granule = 1.0;
+    m.deg = 0;
+    m.n_gr = 1;
+  }
+  m.mu = p->d_mu;
+  m.coef = p->d_coef;
+  if (e != cudaSuccess) {
+    pc_plan_destroy(p);
+    return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
+  }
+  *out = p;
+  return PC_OK;
+}
+
+pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
+  Workspace &w = p->ws;
+  if (n_ic <= w.cap && w.Y[0]) return PC_OK;
+  free_workspace(p);
+  const long long ld = (n_ic + 7) / 8 * 8;
+  if (ld > (1LL << 30)) return PC_EINVAL;
+  const size_t n = p->n, kpad = p->kpad, B = p->model.B;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc(&w.Y[b], n * 6 * ld);
+  if (e == cudaSuccess) e = dalloc(&w.G, kpad * 6 * ld);
+  if (e == cudaSuccess) e = cudaMemset(w.G, 0, sizeof(double) * kpad * 6 * ld);
+  if (e == cudaSuccess && B > 0) e = dalloc(&w.E, n * B * 3 * ld);
+  if (e == cudaSuccess) e = dalloc(&w.Aind, n * 3 * ld);
+  if (e == cudaSuccess) e = cudaMemset(w.Aind, 0, sizeof(double) * n * 3 * ld);
+  // control block: 6 + 7 doubles, 1 u64, 1 i64 and 9 ints per trajectory
+  const size_t bytes = (size_t)ld * (13 * 8 + 8 + 8 + 9 * 4) + 256;
+  if (e == cudaSuccess) e = cudaMalloc(&w.ctl_block, bytes);
+  if (e == cudaSuccess) e = cudaMemset(w.ctl_block, 0, bytes);
+  if (e == cudaSuccess) e = dalloc(&w.done, 2);  // [finished, stopped early]
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&w.h_done, sizeof(int) * 4);
+  for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_workspace(p);
+    return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
+  }
+  char *c = (char *)w.ctl_block;
+  auto take = [&](size_t each) { char *r = c; c += each * ld; return r; };
+  Ctl &t = w.ctl;
+  t.x = (double *)take(8 * 6);
+  t.hbase = (double *)take(8);
+  t.ta = (double *)take(8);
+  t.tb = (double *)take(8);
+  t.w1 = (double *)take(8);
+  t.w2 = (double *)take(8);
+  t.e_best = (double *)take(8);
+  take(8);  // spare double column (keeps the layout at 13 doubles)
+  t.err = (unsigned long long *)take(8);
+  t.p = (long long *)take(8);
+  t.depth = (int *)take(4);
+  t.phase = (int *)take(4);
+  t.status = (int *)take(4);
+  t.sweeps = (int *)take(4);
+  t.seg_sweeps = (int *)take(4);
+  t.nstall = (int *)take(4);
+  t.nseg = (int *)take(4);
+  t.need_setup = (int *)take(4);
+  t.last = (int *)take(4);
+  w.cap = ld;
+  w.ld = (int)ld;
+  return PC_OK;
+}
+
+void pcx::free_workspace(pc_plan *p) {
+  Workspace &w = p->ws;
+  cudaFree(w.Y[0]);
+  cudaFree(w.Y[1]);
+  cudaFree(w.G);
+  cudaFree(w.E);
+  cudaFree(w.Aind);
+  cudaFree(w.ctl_block);
+  cudaFree(w.done);
+  if (w.h_done) cudaFreeHost(w.h_done);
+  for (int i = 0; i < 2; i++)
+    if (w.ev[i]) cudaEventDestroy(w.ev[i]);
+  w = Workspace();
+}
+
+extern "C" void pc_plan_destroy(pc_plan *p) {
+  if (!p) return;
+  free_workspace(p);
+  for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+  cudaFree(p->d_K);
+  cudaFree(p->d_tau);
+  cudaFree(p->d_mu);
+  cudaFree(p->d_coef);
+  std::free(p->h_K);
+  std::free(p->h_tau);
+  delete p;
+}
+
+extern "C" pc_status pc_plan_operator(const pc_plan *p, double *K, double *tau) {
+  if (!p) return PC_EINVAL;
+  if (K) std::memcpy(K, p->h_K, sizeof(double) * p->n * p->n);
+  if (tau) std::memcpy(tau, p->h_tau, sizeof(double) * p->n);
+  return PC_OK;
+}
+
+extern "C" const char *pc_status_string(pc_status s) {
+  switch (s) {
+    case PC_OK: return "success";
+    case PC_EINVAL: return "invalid argument";
+    case PC_ENOMEM: return "out of memory";
+    case PC_ECUDA: return "CUDA runtime error";
+    case PC_ENOTCONV: return "some trajectories stopped before the end of the arc";
+    case PC_ENONFINITE: return "non-finite value";
+  }
+  return "unknown status";
+}

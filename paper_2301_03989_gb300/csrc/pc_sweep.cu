@@ -1,0 +1,626 @@
+// Device kernels of the FP64 batched Picard-Chebyshev sweep and their launchers.
+//
+// One "round" advances every unfinished trajectory by one Picard sweep of its
+// own current segment (Section "Matrix form for vectorized and parallel
+// computation"; Eq. 2):
+//   k_setup    new segments only: node times, ephemeris at the nodes, Keplerian
+//              warm start (Sections "Integration concept", "Dynamics model")
+//   k_force    F = omega2 f(Y, t) at every node (the paper's dynamics kernel)
+//   k_contract Y' = 1 x0^T + K F, the (N+1)x(N+1) by (N+1)x(6M) contraction on
+//              the FP64 tensor cores (DMMA), fused with the per-trajectory
+//              change max_j max(|dr|/|r|, |dv|/|v|) (the paper's errCompute +
+//              maxReduce, Section "CPU-GPU cooperated iteration error
+//              computation", without the host round trip)
+//   k_control  per trajectory: stop test, stall and resolution tests, segment
+//              accept / halve / advance (piecewise integration, Section "Matrix
+//              form")
+// State layout: node-major, component-planar Y[j][c][m] (Section "Dynamics
+// model, array sorting, and CUDA kernel"), leading dimension ld over m.
+#include <cstdint>
+
+#include "pc_internal.h"
+
+namespace pcx {
+namespace {
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// NaN-propagating maximum of non-negative values.
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+__device__ __forceinline__ unsigned long long err_bits(double e) {
+  // non-negative doubles order like their bit patterns; NaN maps to the largest
+  if (e != e) return 0x7FF8000000000000ULL;
+  return (unsigned long long)__double_as_longlong(e);
+}
+
+// ---------------------------------------------------------------------------
+// Segment schedule.  The arc [t0, tf] is measured in units u = hbase / 2^D; a
+// segment at depth d starting at unit p spans 2^(D-d) units and is clipped to
+// end exactly at tf.  Products and sums are rounded one at a time (no fused
+// multiply-add) so every trajectory's segment bounds and node times are the
+// exactly rounded values of these formulas.
+// ---------------------------------------------------------------------------
+__device__ void schedule(const Sweep &s, Ctl &c, int m) {
+  const int D = s.max_depth;
+  const double u = scalbn(c.hbase[m], -D);
+  const long long L = 1LL << (D - c.depth[m]);
+  const long long p = c.p[m];
+  const double ta = dadd(s.t0, dmul(s.sgn, dmul((double)p, u)));
+  double tb;
+  int last = 0;
+  if (dmul((double)(p + L), u) >= s.total) {
+    tb = s.tf;
+    last = 1;
+  } else {
+    tb = dadd(s.t0, dmul(s.sgn, dmul((double)(p + L), u)));
+  }
+  c.ta[m] = ta;
+  c.tb[m] = tb;
+  c.w1[m] = dmul(0.5, dadd(tb, ta));
+  c.w2[m] = dmul(0.5, dsub(tb, ta));
+  c.last[m] = last;
+  c.need_setup[m] = 1;
+  c.seg_sweeps[m] = 0;
+  c.nstall[m] = 0;
+  c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);  // +inf
+}
+
+__global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, int *done) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= s.n_ic) return;
+  const int ld = s.ld;
+  double x[6];
+  bool finite = true;
+  for (int q = 0; q < 6; q++) {
+    x[q] = x0[q * s.n_ic + m];
+    c.x[q * ld + m] = x[q];
+    finite = finite && isfinite(x[q]);
+  }
+  double h = s.total / (double)s.segments;
+  if (s.seg_mode == 1 && finite) {
+    const double r0 = sqrt(dadd(dadd(dmul(x[0], x[0]), dmul(x[1], x[1])), dmul(x[2], x[2])));
+    const double v2 = dadd(dadd(dmul(x[3], x[3]), dmul(x[4], x[4])), dmul(x[5], x[5]));
+    const double alpha = dsub(2.0 / r0, v2 / md.mu_c);
+    if (alpha > 0.0) {
+      const double a = 1.0 / alpha;
+      const double twopi = 6.283185307179586;  // 2 * M_PI rounded
+      h = dmul(twopi, sqrt(dmul(dmul(a, a), a) / md.mu_c)) / (double)s.segments;
+    }
+  }
+  c.hbase[m] = h;
+  c.p[m] = 0;
+  c.depth[m] = 0;
+  c.status[m] = finite ? 0 : PC_IC_NONFINITE;
+  c.sweeps[m] = 0;
+  c.nseg[m] = 0;
+  c.err[m] = 0ULL;
+  c.need_setup[m] = 0;
+  if (!finite || !(s.total > 0.0)) {
+    c.phase[m] = PH_DONE;
+    atomicAdd(done, 1);
+    if (!finite) atomicAdd(done + 1, 1);
+    return;
+  }
+  c.phase[m] = PH_ITER;
+  schedule(s, c, (int)m);
+}
+
+// ---------------------------------------------------------------------------
+// Ephemeris: Clenshaw evaluation of body b at time t,
+//   b_k = c_k + 2 sigma b_{k+1} - b_{k+2},  r = c_0 + sigma b_1 - b_2.
+// Every operation is rounded on its own (no fused multiply-add), so the body
+// positions are the exactly rounded results of this recurrence: near a body
+// the force amplifies a position rounding difference by |r| / |r - r_b|.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ephem_at(const Model &md, double t, int b, double r[3]) {
+  int g = (int)floor((t - md.t_begin) / md.granule);
+  g = g < 0 ? 0 : (g > md.n_gr - 1 ? md.n_gr - 1 : g);
+  const double tg = dadd(md.t_begin, dmul((double)g, md.granule));
+  const double sig = dsub(dmul(2.0, dsub(t, tg)) / md.granule, 1.0);
+  const double s2 = dmul(2.0, sig);
+  const int nc = md.deg + 1;
+  for (int ax = 0; ax < 3; ax++) {
+    const double *cf = md.coef + (((size_t)b * md.n_gr + g) * 3 + ax) * nc;
+    double b1 = 0.0, b2 = 0.0;
+    for (int k = nc - 1; k >= 1; k--) {
+      const double b0 = dsub(dadd(cf[k], dmul(s2, b1)), b2);
+      b2 = b1;
+      b1 = b0;
+    }
+    r[ax] = dsub(dadd(cf[0], dmul(sig, b1)), b2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Keplerian two-body propagation by dt (warm start).  Kepler's equation in the
+// eccentric-anomaly increment X over dt,
+//   n dt = X - (e cos E0) sin X + (e sin E0)(1 - cos X),
+// with e cos E0 = 1 - r0/a and e sin E0 = r0.v0/sqrt(mu a), is solved by
+// Newton's method kept inside the bracket [n dt - 2, n dt + 2], then the
+// Lagrange coefficients map (r0, v0) to (r, v).  Returns false if the orbit
+// is not a bound ellipse or Newton does not settle.
+// ---------------------------------------------------------------------------
+__device__ bool kepler_dt(double mu, const double x0[6], double dt, double out[6]) {
+  const double r0 = sqrt(x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2]);
+  const double vv = x0[3] * x0[3] + x0[4] * x0[4] + x0[5] * x0[5];
+  const double rv = x0[0] * x0[3] + x0[1] * x0[4] + x0[2] * x0[5];
+  const double inv_a = 2.0 / r0 - vv / mu;
+  if (!(inv_a > 0.0)) return false;
+  const double a = 1.0 / inv_a;
+  const double sqrt_a = sqrt(a);
+  const double sqrt_mu = sqrt(mu);
+  const double ecE = 1.0 - r0 * inv_a;
+  const double esE = rv / (sqrt_mu * sqrt_a);
+  const double nm = sqrt_mu * inv_a / sqrt_a;  // sqrt(mu / a^3)
+  const double M = nm * dt;
+  double lo = M - 2.0, hi = M + 2.0, X = M;
+  bool ok = false;
+  for (int it = 0; it < 64; it++) {
+    double sX, cX;
+    sincos(X, &sX, &cX);
+    const double F = X - ecE * sX + esE * (1.0 - cX) - M;
+    if (F > 0.0) hi = X; else lo = X;
+    const double dF = 1.0 - ecE * cX + esE * sX;
+    double Xn = X - F / dF;
+    if (!(Xn > lo && Xn < hi)) Xn = 0.5 * (lo + hi);
+    const double step = fabs(Xn - X);
+    X = Xn;
+    if (step <= 1e-15 * (1.0 + fabs(X))) { ok = true; break; }
+  }
+  if (!ok) return false;
+  double sX, cX;
+  sincos(X, &sX, &cX);
+  const double omc = 1.0 - cX;
+  const double r = a + (r0 - a) * cX + rv / sqrt_mu * sqrt_a * sX;
+  const double f = 1.0 - a / r0 * omc;
+  const double g = a * rv / mu * omc + r0 * sqrt_a / sqrt_mu * sX;
+  const double fd = -sqrt_mu * sqrt_a / (r * r0) * sX;
+  const double gd = 1.0 - a / r * omc;
+  for (int q = 0; q < 3; q++) {
+    out[q] = f * x0[q] + g * x0[3 + q];
+    out[3 + q] = fd * x0[q] + gd * x0[3 + q];
+  }
+  return true;
+}
+
+// Indirect (frame) term of body b: the central body's own acceleration
+// mu_b r_b/|r_b|^3, summed over bodies; it depends on the node time only.
+__device__ __forceinline__ void add_indirect(const Model &md, int b, const double r[3], double ind[3]) {
+  const double d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  const double rs = rsqrt(d2);
+  const double k = md.mu[b] * rs * rs * rs;
+  for (int ax = 0; ax < 3; ax++) ind[ax] = fma(k, r[ax], ind[ax]);
+}
+
+// New segments: node times, body positions and summed indirect term at the
+// nodes, warm start.  Grid: x over trajectories, y over nodes.
+__global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau, double *__restrict__ Y,
+                        double *__restrict__ E, double *__restrict__ Aind) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (m >= s.n_ic) return;
+  if (c.phase[m] != PH_ITER || !c.need_setup[m]) return;
+  const int ld = s.ld, B = md.B;
+  const double t = dadd(c.w1[m], dmul(c.w2[m], tau[j]));
+  double ind[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < B; b++) {
+    double r[3];
+    ephem_at(md, t, b, r);
+    for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
+    if (md.indirect) add_indirect(md, b, r, ind);
+  }
+  for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
+  double x0[6], y[6];
+  for (int q = 0; q < 6; q++) x0[q] = c.x[q * ld + m];
+  bool ok = false;
+  if (j > 0 && s.warm) ok = kepler_dt(md.mu_c, x0, dsub(t, c.ta[m]), y);
+  for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = ok ? y[q] : x0[q];
+}
+
+// ---------------------------------------------------------------------------
+// Force: F[j][.][m] = omega2 * (v, a(r, t_j)).  One thread per (node, trajectory).
+// ---------------------------------------------------------------------------
+// Body b's position component ax is Eb[(b*3 + ax) * es]; the summed indirect
+// term component ax is Ai[ax * es].
+__device__ __forceinline__ void accel(const Model &md, const double *__restrict__ Eb, const double *__restrict__ Ai,
+                                      size_t es, const double r[3], double a[3]) {
+  const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  const double rs = rsqrt(r2);
+  const double kc = md.mu_c * rs * rs * rs;
+  a[0] = -kc * r[0];
+  a[1] = -kc * r[1];
+  a[2] = -kc * r[2];
+  for (int b = 0; b < md.B; b++) {
+    const double d0 = r[0] - Eb[(size_t)(b * 3 + 0) * es];
+    const double d1 = r[1] - Eb[(size_t)(b * 3 + 1) * es];
+    const double d2 = r[2] - Eb[(size_t)(b * 3 + 2) * es];
+    const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+    const double ds = rsqrt(dd);
+    const double kb = md.mu[b] * ds * ds * ds;
+    a[0] -= kb * d0;
+    a[1] -= kb * d1;
+    a[2] -= kb * d2;
+  }
+  if (md.indirect) {
+    a[0] -= Ai[0];
+    a[1] -= Ai[es];
+    a[2] -= Ai[2 * es];
+  }
+}
+
+__global__ void k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y, const double *__restrict__ E,
+                        const double *__restrict__ Aind, double *__restrict__ G) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (m >= s.n_ic || c.phase[m] != PH_ITER) return;
+  const int ld = s.ld;
+  const double w2 = c.w2[m];
+  const size_t yb = (size_t)j * 6 * ld + m;
+  const double r[3] = {Y[yb], Y[yb + ld], Y[yb + 2 * (size_t)ld]};
+  double a[3];
+  accel(md, E + (size_t)j * md.B * 3 * ld + m, Aind + (size_t)j * 3 * ld + m, (size_t)ld, r, a);
+  G[yb] = w2 * Y[yb + 3 * (size_t)ld];
+  G[yb + ld] = w2 * Y[yb + 4 * (size_t)ld];
+  G[yb + 2 * (size_t)ld] = w2 * Y[yb + 5 * (size_t)ld];
+  G[yb + 3 * (size_t)ld] = w2 * a[0];
+  G[yb + 4 * (size_t)ld] = w2 * a[1];
+  G[yb + 5 * (size_t)ld] = w2 * a[2];
+}
+
+// ---------------------------------------------------------------------------
+// Contraction on the FP64 tensor cores: mma.sync m16n8k4 f64.
+// One warp computes output nodes j = 1 + 16*rt + (0..15) for 8 trajectories
+// m0..m0+7 and all six components (six 16x8 accumulators), streaming
+// K[rows][k] and G[k][c][m] fragments straight from L2/L1 -- FP64 throughput,
+// not bandwidth, bounds this kernel.  Fragment layouts (PTX ISA, mma.m16n8k4
+// .f64): with g = lane/4, t = lane%4:  A: a0 = A[g][t], a1 = A[g+8][t];
+// B: b0 = B[t][g];  C: c0,c1 = C[g][2t..2t+1], c2,c3 = C[g+8][2t..2t+1].
+// Epilogue: Y' = x0 + acc, and (unless DIAG) the per-trajectory maximum
+// change, reduced over the warp and merged with atomicMax.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dmma16x8x4(double (&d)[4], double a0, double a1, double b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+      : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+      : "d"(a0), "d"(a1), "d"(b0));
+}
+
+template <bool DIAG>
+__global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *__restrict__ K,
+                                                  const double *__restrict__ G, const double *__restrict__ Yold,
+                                                  double *__restrict__ Ynew) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_rt = s.rows_pad / 16;
+  const int rt = warp % n_rt;
+  const int ct = warp / n_rt;
+  const int m0 = ct * 8;
+  if (m0 >= s.ld) return;
+  const int g = lane >> 2, t = lane & 3;
+  const int ld = s.ld;
+  bool mine_active = false;
+  if (!DIAG) {
+    const int mm = m0 + g;
+    mine_active = (mm < s.n_ic) && c.phase[mm] == PH_ITER;
+    if (!__any_sync(0xffffffffu, mine_active)) return;
+  }
+  double acc[6][4];
+#pragma unroll
+  for (int q = 0; q < 6; q++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[q][i] = 0.0;
+  const double *Ka = K + (size_t)(rt * 16 + g) * s.kpad + t;
+  const double *Kb = Ka + (size_t)8 * s.kpad;
+  const double *Gp = G + (size_t)t * 6 * ld + m0 + g;
+  const size_t gstep = (size_t)4 * 6 * ld;
+  for (int k0 = 0; k0 < s.kpad; k0 += 4) {
+    const double a0 = __ldg(Ka + k0), a1 = __ldg(Kb + k0);
+#pragma unroll
+    for (int q = 0; q < 6; q++) dmma16x8x4(acc[q], a0, a1, __ldg(Gp + (size_t)q * ld));
+    Gp += gstep;
+  }
+  // epilogue
+  double emax[2] = {0.0, 0.0};
+#pragma unroll
+  for (int h = 0; h < 2; h++) {          // row g (h=0) or g+8 (h=1)
+    const int j = 1 + rt * 16 + g + 8 * h;
+#pragma unroll
+    for (int e = 0; e < 2; e++) {        // column 2t+e
+      const int m = m0 + 2 * t + e;
+      if (j > s.N || m >= s.n_ic) continue;
+      if (!DIAG && c.phase[m] != PH_ITER) continue;
+      double yn[6];
+      const size_t base = (size_t)j * 6 * ld + m;
+#pragma unroll
+      for (int q = 0; q < 6; q++) {
+        yn[q] = c.x[q * ld + m] + acc[q][2 * h + e];
+        Ynew[base + (size_t)q * ld] = yn[q];
+      }
+      if (!DIAG) {
+        double d[6];
+#pragma unroll
+        for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
+        double dr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double dv = sqrt(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+        if (s.relative) {
+          const double nr = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+          const double nv = sqrt(yn[3] * yn[3] + yn[4] * yn[4] + yn[5] * yn[5]);
+          if (nr > 0.0) dr = dr / nr;
+          if (nv > 0.0) dv = dv / nv;
+        }
+        emax[e] = nanmax(emax[e], nanmax(dr, dv));
+      }
+    }
+  }
+  // node 0 is the segment's initial state
+  if (rt == 0 && g == 0) {
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      const int m = m0 + 2 * t + e;
+      if (m < s.n_ic && (DIAG || c.phase[m] == PH_ITER))
+#pragma unroll
+        for (int q = 0; q < 6; q++) Ynew[(size_t)q * ld + m] = c.x[q * ld + m];
+    }
+  }
+  if (!DIAG) {
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      double v = emax[e];
+      v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 4));
+      v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 8));
+      v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 16));
+      const int m = m0 + 2 * t + e;
+      if (g == 0 && m < s.n_ic && c.phase[m] == PH_ITER) atomicMax(c.err + m, err_bits(v));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Resolution test (Chebyshev tail of the force fit).  On the CGL nodes
+// T_N(tau_j) = (-1)^(N+j) and T_{N-1}(tau_j) = (-1)^(N+j) tau_j, so the two
+// top coefficients of the interpolant of g are
+//   a_N = (1/N) sum''_j (-1)^(N+j) g_j,   a_{N-1} = (2/N) sum''_j (-1)^(N+j) tau_j g_j
+// (sum'' halves the end terms).  The integrated error is about
+// 2 |omega2| (|a_{N-1}| + |a_N|) per unit of g; G already carries omega2.
+// Position components are measured against max_j |r_j|, velocity ones against
+// max_j |v_j| (relative mode).
+// ---------------------------------------------------------------------------
+__device__ double tail_estimate(const Sweep &s, const double *__restrict__ tau, const double *__restrict__ G,
+                                const double *__restrict__ Y, int m) {
+  const int ld = s.ld, N = s.N;
+  double sN[6] = {0, 0, 0, 0, 0, 0}, sN1[6] = {0, 0, 0, 0, 0, 0};
+  double rmax = 0.0, vmax = 0.0;
+  for (int j = 0; j <= N; j++) {
+    const double w = (j == 0 || j == N) ? 0.5 : 1.0;
+    const double sg = ((N + j) & 1) ? -w : w;
+    const double tj = tau[j] * sg;
+    const size_t base = (size_t)j * 6 * ld + m;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      const double gq = G[base + (size_t)q * ld];
+      sN[q] = fma(sg, gq, sN[q]);
+      sN1[q] = fma(tj, gq, sN1[q]);
+    }
+    if (s.relative) {
+      const double y0 = Y[base], y1 = Y[base + ld], y2 = Y[base + 2 * (size_t)ld];
+      const double y3 = Y[base + 3 * (size_t)ld], y4 = Y[base + 4 * (size_t)ld], y5 = Y[base + 5 * (size_t)ld];
+      rmax = fmax(rmax, sqrt(y0 * y0 + y1 * y1 + y2 * y2));
+      vmax = fmax(vmax, sqrt(y3 * y3 + y4 * y4 + y5 * y5));
+    }
+  }
+  double er = 0.0, ev = 0.0;
+#pragma unroll
+  for (int q = 0; q < 6; q++) {
+    const double tl = 2.0 * (fabs(2.0 * sN1[q] / N) + fabs(sN[q] / N));
+    if (q < 3) er = nanmax(er, tl); else ev = nanmax(ev, tl);
+  }
+  if (s.relative) {
+    if (rmax > 0.0) er /= rmax;
+    if (vmax > 0.0) ev /= vmax;
+  }
+  return nanmax(er, ev);
+}
+
+// Per-trajectory decisions after a sweep.  Same rules, same order as the
+// oracle: blow-up, tolerance, stall, cap; then the resolution test on an
+// accepted segment; accept (advance, grow one level) or fail (halve).
+__global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const double *__restrict__ G,
+                          const double *__restrict__ Ynew, int *done) {
+  const long long mm = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (mm >= s.n_ic) return;
+  const int m = (int)mm;
+  if (c.phase[m] != PH_ITER) return;
+  const int ld = s.ld;
+  c.need_setup[m] = 0;
+  const double e = __longlong_as_double((long long)c.err[m]);
+  c.err[m] = 0ULL;
+  const int ss = ++c.seg_sweeps[m];
+  c.sweeps[m] += 1;
+  int out = SEG_CONTINUE;
+  if (!(e <= s.div_limit)) {
+    out = SEG_FAIL_DIV;
+  } else if (e < s.tol) {
+    out = SEG_OK;
+  } else {
+    if (e < c.e_best[m]) {
+      c.e_best[m] = e;
+      c.nstall[m] = 0;
+    } else {
+      c.nstall[m] += 1;
+    }
+    if (c.nstall[m] >= s.stall_sweeps && c.e_best[m] < s.stall_factor * s.tol) out = SEG_STALLED;
+    else if (ss >= s.max_iters) out = SEG_FAIL_CAP;
+  }
+  if (out == SEG_CONTINUE) return;
+  if ((out == SEG_OK || out == SEG_STALLED) && s.trunc_tol > 0.0 && tail_estimate(s, tau, G, Ynew, m) > s.trunc_tol)
+    out = SEG_FAIL_TRUNC;
+  const int D = s.max_depth;
+  bool accept = (out == SEG_OK || out == SEG_STALLED);
+  if (out == SEG_FAIL_TRUNC && c.depth[m] >= D) {
+    accept = true;
+    c.status[m] |= PC_IC_UNRESOLVED;
+  }
+  if (accept) {
+    if (out == SEG_STALLED) c.status[m] |= PC_IC_STALLED;
+    const int k = c.nseg[m];
+    if (s.ckpt && k < s.max_ckpt) {
+      double *ck = s.ckpt + ((size_t)m * s.max_ckpt + k) * 7;
+      ck[0] = c.ta[m];
+      for (int q = 0; q < 6; q++) ck[1 + q] = c.x[q * ld + m];
+    }
+    const size_t last_row = (size_t)s.N * 6 * ld + m;
+    for (int q = 0; q < 6; q++) c.x[q * ld + m] = Ynew[last_row + (size_t)q * ld];
+    c.nseg[m] = k + 1;
+    c.p[m] += 1LL << (D - c.depth[m]);
+    if (c.last[m]) {
+      c.phase[m] = PH_DONE;
+      atomicAdd(done, 1);
+      return;
+    }
+    if (c.depth[m] > 0) c.depth[m] -= 1;
+    schedule(s, c, m);
+  } else {
+    c.depth[m] += 1;
+    if (c.depth[m] > D) {
+      c.status[m] |= (out == SEG_FAIL_DIV) ? PC_IC_NONFINITE : PC_IC_NOT_CONVERGED;
+      c.phase[m] = PH_DONE;
+      atomicAdd(done, 1);
+      atomicAdd(done + 1, 1);
+      return;
+    }
+    schedule(s, c, m);
+  }
+}
+
+__global__ void k_finish(Sweep s, Ctl c, double *__restrict__ xf, int *__restrict__ status, int *__restrict__ iters,
+                         int *__restrict__ nseg, int abort_rest) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= s.n_ic) return;
+  if (abort_rest && c.phase[m] != PH_DONE) {
+    c.status[m] |= PC_IC_NOT_CONVERGED;
+    c.phase[m] = PH_DONE;
+  }
+  for (int q = 0; q < 6; q++) xf[q * s.n_ic + m] = c.x[q * s.ld + m];
+  if (status) status[m] = c.status[m];
+  if (iters) iters[m] = c.sweeps[m];
+  if (nseg) nseg[m] = c.nseg[m];
+}
+
+// ---- kernel-level diagnostics ------------------------------------------------
+__global__ void k_eval_ephem(Model md, long long n, const double *__restrict__ t, double *__restrict__ rb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int b = 0; b < md.B; b++) {
+    double r[3];
+    ephem_at(md, t[i], b, r);
+    for (int ax = 0; ax < 3; ax++) rb[(size_t)(b * 3 + ax) * n + i] = r[ax];
+  }
+}
+
+__global__ void k_eval_warm(Model md, long long n, const double *__restrict__ x0, const double *__restrict__ dt,
+                            double *__restrict__ x) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[6], y[6];
+  for (int q = 0; q < 6; q++) a[q] = x0[q * n + i];
+  const bool ok = kepler_dt(md.mu_c, a, dt[i], y);
+  for (int q = 0; q < 6; q++) x[q * n + i] = ok ? y[q] : a[q];
+}
+
+__global__ void k_eval_dyn(Model md, long long n, const double *__restrict__ t, const double *__restrict__ y,
+                           double *__restrict__ f) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double rb[kMaxBodies * 3];
+  double ind[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < md.B; b++) {
+    ephem_at(md, t[i], b, rb + 3 * b);
+    if (md.indirect) add_indirect(md, b, rb + 3 * b, ind);
+  }
+  const double r[3] = {y[i], y[n + i], y[2 * n + i]};
+  double a[3];
+  accel(md, rb, ind, 1, r, a);
+  for (int q = 0; q < 3; q++) {
+    f[q * n + i] = y[(3 + q) * n + i];
+    f[(3 + q) * n + i] = a[q];
+  }
+}
+
+constexpr int kThreads = 128;
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---- launchers ----------------------------------------------------------------
+cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cudaStream_t st) {
+  const Workspace &w = p->ws;
+  cudaError_t e = cudaMemsetAsync(w.done, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_init<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, w.ctl, p->model, x0, w.done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t st, cudaEvent_t *ev) {
+  const Workspace &w = p->ws;
+  double *Yc = w.Y[cur], *Yn = w.Y[cur ^ 1];
+  const dim3 gnode(blocks_for(s.n_ic, kThreads), s.n);
+  if (ev) cudaEventRecord(ev[0], st);
+  k_setup<<<gnode, kThreads, 0, st>>>(s, w.ctl, p->model, p->d_tau, Yc, w.E, w.Aind);
+  if (ev) cudaEventRecord(ev[1], st);
+  k_force<<<gnode, kThreads, 0, st>>>(s, w.ctl, p->model, Yc, w.E, w.Aind, w.G);
+  if (ev) cudaEventRecord(ev[2], st);
+  const long long warps = (long long)(s.rows_pad / 16) * (s.ld / 8);
+  k_contract<false><<<blocks_for(warps * 32, 256), 256, 0, st>>>(s, w.ctl, p->d_K, w.G, Yc, Yn);
+  if (ev) cudaEventRecord(ev[3], st);
+  k_control<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, w.ctl, p->d_tau, w.G, Yn, w.done);
+  if (ev) cudaEventRecord(ev[4], st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const pc_plan *p, const Sweep &s, double *xf, int *status, int *iters, int *nseg,
+                          int abort_rest, cudaStream_t st) {
+  k_finish<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, p->ws.ctl, xf, status, iters, nseg, abort_rest);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_ephemeris(const pc_plan *p, long long n, const double *t, double *rb, cudaStream_t st) {
+  k_eval_ephem<<<blocks_for(n, kThreads), kThreads, 0, st>>>(p->model, n, t, rb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_warm(const pc_plan *p, long long n, const double *x0, const double *dt, double *x,
+                             cudaStream_t st) {
+  k_eval_warm<<<blocks_for(n, kThreads), kThreads, 0, st>>>(p->model, n, x0, dt, x);
+  return cudaGetLastError();
+}
+
+// Dynamics at n points with the same device functions as the sweep
+// (ephemeris, indirect term, acceleration); omega2 = 1.
+cudaError_t launch_eval_dynamics(const pc_plan *p, long long n, const double *t, const double *y, double *f,
+                                 cudaStream_t st) {
+  k_eval_dyn<<<blocks_for(n, kThreads), kThreads, 0, st>>>(p->model, n, t, y, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_operator(const pc_plan *p, long long n_ic, int ld, const double *x0, const double *G,
+                                  double *Y, cudaStream_t st) {
+  const Workspace &w = p->ws;
+  Sweep s{};
+  s.N = p->N;
+  s.n = p->n;
+  s.kpad = p->kpad;
+  s.rows_pad = p->rows_pad;
+  s.n_ic = n_ic;
+  s.ld = ld;
+  Ctl c = w.ctl;
+  c.x = const_cast<double *>(x0);
+  const long long warps = (long long)(s.rows_pad / 16) * (s.ld / 8);
+  k_contract<true><<<blocks_for(warps * 32, 256), 256, 0, st>>>(s, c, p->d_K, G, nullptr, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace pcx

@@ -1,0 +1,129 @@
+"""Kernel-level parity: each device kernel of the sweep, run through the C ABI,
+against the CPU oracle's routine on the same seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_2301_03989_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    import torch
+    from paper_2301_03989_gb300 import build, pcprop
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return pcprop
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return W.config2(M=64)
+
+
+def _dev(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("N", [16, 64, 128, 256])
+@pytest.mark.parametrize("truncated", [0, 1])
+def test_operator_matches_oracle(pc, ora, N, truncated):
+    plan = pc.plan_create(N, 4, W.MU_SUN, [], options=pc.options_default(truncated=truncated))
+    K, tau = pc.plan_operator(plan)
+    np.testing.assert_array_equal(tau, ora.cgl_nodes(N))
+    np.testing.assert_allclose(K, ora.pc_operator(N, bool(truncated)), rtol=0, atol=2e-16 * max(1, N // 32))
+    plan.close()
+
+
+@pytest.mark.parametrize("N", [16, 64, 128, 256])
+@pytest.mark.parametrize("M", [1, 3, 33, 1000])
+def test_contraction_dmma_vs_oracle_operator(pc, ora, N, M):
+    """The DMMA contraction y = x0 + K g against the oracle's K applied in FP64
+    (numpy matmul), several row tiles, column tiles and a ragged tail."""
+    import torch
+    rng = np.random.default_rng(N * 1000 + M)
+    plan = pc.plan_create(N, 4, W.MU_SUN, [])
+    x0 = rng.standard_normal((6, M)) * 1e8
+    g = rng.standard_normal((N + 1, 6, M)) * 1e6
+    y = torch.zeros((N + 1, 6, M), dtype=torch.float64, device="cuda")
+    pc.apply_operator(plan, _dev(x0), _dev(g), y)
+    torch.cuda.synchronize()
+    K = ora.pc_operator(N)
+    ref = x0[None] + np.einsum("jk,kcm->jcm", K, g)
+    scale = np.abs(K).sum(1).max() * 1e6
+    np.testing.assert_allclose(y.cpu().numpy(), ref, rtol=0, atol=4e-16 * (scale + 1e8))
+    np.testing.assert_array_equal(y.cpu().numpy()[0], x0)
+    plan.close()
+
+
+def test_ephemeris_vs_oracle(pc, ora, cfg2):
+    import torch
+    plan = pc.plan_from_workload(cfg2)
+    m = ora.Model.from_workload(cfg2)
+    rng = np.random.default_rng(5)
+    t = np.concatenate([rng.uniform(cfg2.t0, cfg2.tf, 997),
+                        cfg2.t_begin + cfg2.granule * np.arange(3, 9)])       # boundary ties
+    B = len(cfg2.mu)
+    rb = torch.zeros((B, 3, t.size), dtype=torch.float64, device="cuda")
+    pc.eval_ephemeris(plan, _dev(t), rb)
+    got = rb.cpu().numpy()
+    ref = np.stack([ora.ephem_eval(m, ti) for ti in t], axis=-1)          # [B][3][n]
+    np.testing.assert_array_equal(got, ref)        # same recurrence, each step rounded alike
+    plan.close()
+
+
+def test_dynamics_vs_oracle(pc, ora, cfg2):
+    """Force at states near and far from the bodies (including 1e4 km from Venus)."""
+    import torch
+    plan = pc.plan_from_workload(cfg2)
+    m = ora.Model.from_workload(cfg2)
+    o = ora.Opts()
+    rng = np.random.default_rng(6)
+    n = 515
+    t = rng.uniform(cfg2.t0, cfg2.tf, n)
+    y = np.zeros((6, n))
+    for i in range(n):
+        rb = ora.ephem_eval(m, t[i])
+        if i % 5 == 0:
+            d = rng.standard_normal(3)
+            y[:3, i] = rb[1] + d / np.linalg.norm(d) * rng.uniform(1e4, 1e6)
+        else:
+            y[:3, i] = rng.standard_normal(3) * 1.5e8
+        y[3:, i] = rng.standard_normal(3) * 30.0
+    f = torch.zeros((6, n), dtype=torch.float64, device="cuda")
+    pc.eval_dynamics(plan, _dev(t), _dev(y), f)
+    got = f.cpu().numpy()
+    for i in range(n):
+        ref = ora.dynamics(m, o, t[i], y[:, i])
+        np.testing.assert_array_equal(got[:3, i], ref[:3])
+        # rounding bound: a few ulps of each term's magnitude (direct and indirect)
+        rb = ora.ephem_eval(m, t[i])
+        r = y[:3, i]
+        mag = W.MU_SUN / (r @ r) + sum(mu / ((r - p) @ (r - p)) + mu / (p @ p) for mu, p in zip(cfg2.mu, rb))
+        np.testing.assert_allclose(got[3:, i], ref[3:], rtol=0, atol=2e-15 * mag)
+    plan.close()
+
+
+def test_warm_start_vs_oracle_kepler(pc, ora):
+    import torch
+    plan = pc.plan_create(16, 4, W.MU_SUN, [])
+    rng = np.random.default_rng(7)
+    n = 300
+    x0 = np.zeros((6, n))
+    dt = rng.uniform(-3e7, 3e7, n)
+    for i in range(n):
+        x0[:, i] = W.elements_to_state(rng.uniform(0.3, 5) * W.AU, rng.uniform(0, 0.9), rng.uniform(0, 3),
+                                       rng.uniform(0, 6), rng.uniform(0, 6), rng.uniform(0, 6), W.MU_SUN)
+    x0[:, -1] = [1e8, 0, 0, 0, 60.0, 0]       # hyperbolic: copied unchanged (cold start)
+    x = torch.zeros((6, n), dtype=torch.float64, device="cuda")
+    pc.eval_warm_start(plan, _dev(x0), _dev(dt), x)
+    got = x.cpu().numpy()
+    for i in range(n - 1):
+        ref, rc = ora.kepler(W.MU_SUN, x0[:, i], dt[i])
+        assert rc == 0
+        np.testing.assert_allclose(got[:3, i], ref[:3], rtol=0, atol=1e-11 * np.linalg.norm(ref[:3]))
+        np.testing.assert_allclose(got[3:, i], ref[3:], rtol=0, atol=1e-11 * np.linalg.norm(ref[3:]))
+    np.testing.assert_array_equal(got[:, -1], x0[:, -1])
+    plan.close()

@@ -1,0 +1,189 @@
+"""End-to-end parity of the FP64 GPU sweep (pc_propagate through the C ABI)
+against the CPU oracle on the same seeded inputs.
+
+Tolerance: positions and velocities within 1e-10 relative (per trajectory,
+|x_gpu - x_oracle| / |x_oracle| for r and v separately).  Through a close
+flyby the oracle-vs-GPU round-off difference (~1e-15 per sweep, the two sum the
+contraction in different orders) is amplified by the flyby's state-transition
+matrix, so multi-year flyby arcs are compared segment by segment: the oracle
+restarts each accepted segment from the GPU's own checkpoint and must land on
+the GPU's next checkpoint within 1e-10.
+"""
+import numpy as np
+import pytest
+
+from paper_2301_03989_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pc():
+    import torch
+    from paper_2301_03989_gb300 import build, pcprop
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return pcprop
+
+
+def _dev(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def run_gpu(pc, w, x0, t0=None, tf=None, max_ckpt=0, **opts):
+    import torch
+    t0 = w.t0 if t0 is None else t0
+    tf = w.tf if tf is None else tf
+    plan = pc.plan_from_workload(w, **opts)
+    M = x0.shape[0]
+    xd = _dev(W.to_planar(x0))
+    xf = torch.zeros_like(xd)
+    st = torch.zeros(M, dtype=torch.int32, device="cuda")
+    it = torch.zeros(M, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(M, dtype=torch.int32, device="cuda")
+    ck = torch.zeros((M, max(max_ckpt, 1), 7), dtype=torch.float64, device="cuda") if max_ckpt else None
+    code, rounds = pc.propagate(plan, xd, t0, tf, xf, status=st, iters=it, nseg=ns, ckpt=ck, max_ckpt=max_ckpt)
+    torch.cuda.synchronize()
+    out = dict(code=code, rounds=rounds, xf=W.from_planar(xf.cpu().numpy()), status=st.cpu().numpy(),
+               iters=it.cpu().numpy(), nseg=ns.cpu().numpy())
+    if ck is not None:
+        out["ckpt"] = ck.cpu().numpy()
+    plan.close()
+    return out
+
+
+def run_oracle(ora, w, x0, t0=None, tf=None, threads=8, max_ckpt=0, **opts):
+    m = ora.Model.from_workload(w)
+    kw = dict(N=w.N, segments=w.segments, seg_mode=w.seg_mode, tol=w.tol, max_iters=w.max_iters,
+              max_depth=w.max_depth)
+    kw.update(opts)
+    o = ora.Opts(**kw)
+    return ora.propagate(m, o, x0, w.t0 if t0 is None else t0, w.tf if tf is None else tf, threads=threads,
+                         max_ckpt=max_ckpt)
+
+
+def rel_err(a, b):
+    er = np.linalg.norm(a[:, :3] - b[:, :3], axis=1) / np.linalg.norm(b[:, :3], axis=1)
+    ev = np.linalg.norm(a[:, 3:] - b[:, 3:], axis=1) / np.linalg.norm(b[:, 3:], axis=1)
+    return er, ev
+
+
+def test_config1_full(pc, ora):
+    """Sun + Venus + Earth, 64 ICs, one revolution in 8 segments, N = 64, tol 1e-13."""
+    w = W.config1()
+    g = run_gpu(pc, w, w.x0)
+    o = run_oracle(ora, w, w.x0)
+    assert g["code"] == pc.PC_OK
+    er, ev = rel_err(g["xf"], o["xf"])
+    assert er.max() < TOL and ev.max() < TOL, (er.max(), ev.max())
+    np.testing.assert_array_equal(g["status"], o["status"])
+    np.testing.assert_array_equal(g["nseg"], o["nseg"])
+    assert np.abs(g["iters"] - o["iters"]).max() <= 2
+
+
+@pytest.mark.parametrize("M", [1, 3, 33])
+def test_config1_ragged_batches_and_batch_invariance(pc, ora, M):
+    """Ragged batch sizes; every trajectory's result is independent of the batch
+    it is in (augmentation invariance): bitwise equal to the 64-IC run."""
+    w = W.config1()
+    full = run_gpu(pc, w, w.x0)
+    part = run_gpu(pc, w, w.x0[:M])
+    np.testing.assert_array_equal(part["xf"], full["xf"][:M])
+    np.testing.assert_array_equal(part["iters"], full["iters"][:M])
+
+
+def test_config1_backward(pc, ora):
+    w = W.config1(M=8)
+    g = run_gpu(pc, w, w.x0, t0=w.tf, tf=w.t0)
+    o = run_oracle(ora, w, w.x0, t0=w.tf, tf=w.t0)
+    er, ev = rel_err(g["xf"], o["xf"])
+    assert er.max() < TOL and ev.max() < TOL
+
+
+def test_config2_short_arc_end_to_end(pc, ora):
+    """Sun + 8 planets + Moon, close Venus flybys: 20 days through the flyby,
+    end-to-end within 1e-10 (the STM over 20 days stays small)."""
+    w = W.config2(M=48)
+    tf = 20 * W.DAY
+    g = run_gpu(pc, w, w.x0, tf=tf)
+    o = run_oracle(ora, w, w.x0, tf=tf)
+    er, ev = rel_err(g["xf"], o["xf"])
+    assert er.max() < TOL and ev.max() < TOL, (er.max(), ev.max())
+    np.testing.assert_array_equal(g["nseg"], o["nseg"])
+    assert (g["nseg"] > 3).all()        # the flyby forced halving
+
+
+def _segment_local(ora, w, g, idx):
+    """Oracle restarted at the GPU's checkpoints; returns max relative error at
+    the next checkpoint (or the end state)."""
+    m = ora.Model.from_workload(w)
+    o = ora.Opts(N=w.N, segments=1, seg_mode=0, tol=w.tol, max_iters=w.max_iters, max_depth=0, trunc_tol=0.0)
+    worst = 0.0
+    for i in idx:
+        ns = int(g["nseg"][i])
+        ck = g["ckpt"][i]
+        for s in range(ns):
+            ta, xa = ck[s, 0], ck[s, 1:]
+            if s + 1 < ns:
+                tb, xb = ck[s + 1, 0], ck[s + 1, 1:]
+            else:
+                tb, xb = w.tf, g["xf"][i]
+            r = ora.propagate(m, o, xa[None], ta, tb)
+            er, ev = rel_err(r["xf"], xb[None])
+            worst = max(worst, er[0], ev[0])
+    return worst
+
+
+def test_config2_full_arc_segment_local(pc, ora):
+    """16 ICs over the full 4-year arc: statuses agree; each GPU segment matches
+    the oracle's segment started from the same checkpoint."""
+    w = W.config2(M=16)
+    g = run_gpu(pc, w, w.x0, max_ckpt=600)
+    assert g["code"] == pc.PC_OK
+    assert (g["nseg"] < 600).all()
+    assert _segment_local(ora, w, g, range(16)) < TOL
+    o = run_oracle(ora, w, w.x0)
+    np.testing.assert_array_equal(g["status"], o["status"])
+    er, ev = rel_err(g["xf"], o["xf"])
+    # end to end the flyby amplifies round-off; report-only bound
+    assert er.max() < 1e-6 and ev.max() < 1e-6
+
+
+def test_config2_full_size_sampled(pc, ora):
+    """The full 4096-IC, 4-year workload in the benchmark's launch
+    configuration; sampled trajectories checked segment by segment."""
+    w = W.config2()
+    g = run_gpu(pc, w, w.x0, max_ckpt=600)
+    assert g["code"] == pc.PC_OK
+    assert (g["status"] & (pc.PC_IC_NOT_CONVERGED | pc.PC_IC_NONFINITE) == 0).all()
+    idx = np.random.default_rng(11).choice(w.n_ic, 6, replace=False)
+    assert _segment_local(ora, w, g, idx) < TOL
+
+
+def test_edge_cases(pc, ora):
+    import torch
+    w = W.config1(M=4)
+    x = w.x0.copy()
+    x[2, 4] = np.nan
+    g = run_gpu(pc, w, x)
+    assert g["code"] == pc.PC_ENOTCONV
+    assert g["status"][2] == pc.PC_IC_NONFINITE and g["status"][0] == 0
+    # tolerance 0: nothing converges, every halving fails -> NOT_CONVERGED
+    g = run_gpu(pc, w, w.x0[:2], tol=0.0, max_iters=6, max_depth=1)
+    o = run_oracle(ora, w, w.x0[:2], tol=0.0, max_iters=6, max_depth=1)
+    assert g["code"] == pc.PC_ENOTCONV
+    np.testing.assert_array_equal(g["status"], o["status"])
+    # zero-length arc
+    g = run_gpu(pc, w, w.x0, t0=5.0, tf=5.0)
+    np.testing.assert_array_equal(g["xf"], w.x0)
+    # invalid arguments
+    plan = pc.plan_from_workload(w)
+    xd = _dev(W.to_planar(w.x0))
+    with pytest.raises(pc.PCError) as e:
+        pc.propagate(plan, xd, 0.0, 1e12, torch.zeros_like(xd))      # beyond the ephemeris table
+    assert e.value.code == pc.PC_EINVAL
+    assert pc.lib().pc_propagate(plan.handle, 4, None, 0.0, 1.0, 0.0, None, None, None, None) == pc.PC_EINVAL
+    assert pc.lib().pc_propagate(plan.handle, 0, None, 0.0, 1.0, 0.0, None, None, None, None) == pc.PC_OK
+    plan.close()
