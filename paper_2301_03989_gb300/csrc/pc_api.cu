@@ -61,16 +61,27 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
   s.trunc_tol = o.trunc_tol;
   s.max_ckpt = max_ckpt;
   s.ckpt = max_ckpt > 0 ? ckpt : nullptr;
-
   Workspace &w = p->ws;
+  s.xf = xf;
+  s.status = status;
+  s.iters = iters;
+  s.nseg = nseg;
+  s.list[0] = w.lists;
+  s.list[1] = w.lists + w.ld;
+  s.list_cnt = w.ints + 2;
+  s.list_cur = 0;
+  s.A = (int)n_ic;
+  w.live = 0;
+
   cudaError_t e = launch_init(p, s, x0, st);
   const long long max_rounds = o.max_rounds > 0 ? o.max_rounds : 10000000LL;
   long long rounds = 0;
   int cur = 0;
-  int pending = -1;  // slot of the batch whose counter copy is in flight
+  int pending = -1;         // slot of the batch whose counter copy is in flight
+  int done_known = 0;       // finished trajectories at the last completed check
   bool finished = false, capped = false;
   while (e == cudaSuccess && !finished) {
-    for (int r = 0; r < kRoundsPerBatch && e == cudaSuccess; r++) {
+    for (int r = 0; r < kRoundsPerBatch && e == cudaSuccess && s.A > 0; r++) {
       cudaEvent_t *ev = nullptr;
       if (p->prof_on) {
         const size_t need = (size_t)(p->prof_rounds + 1) * 5;
@@ -85,30 +96,49 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
       }
       e = launch_round(p, s, cur, st, ev);
       cur ^= 1;
+      s.list_cur ^= 1;
       rounds++;
     }
     if (e != cudaSuccess) break;
     const int slot = (pending < 0) ? 0 : (pending ^ 1);
-    e = cudaMemcpyAsync(w.h_done + 2 * slot, w.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(w.h_ints + 8 * slot, w.ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecord(w.ev[slot], st);
     if (e != cudaSuccess) break;
     if (pending >= 0) {
       e = cudaEventSynchronize(w.ev[pending]);
-      if (e == cudaSuccess && w.h_done[2 * pending] >= n_ic) finished = true;
+      if (e != cudaSuccess) break;
+      done_known = w.h_ints[8 * pending];
+      if (done_known >= n_ic) finished = true;
     }
     pending = slot;
-    if (!finished && rounds >= max_rounds) {
+    if (finished) break;
+    if (rounds >= max_rounds) {
       capped = true;
       break;
     }
+    // Compaction: when at least 1/8 of the slots hold finished trajectories,
+    // move the active ones to the front so later rounds launch over fewer slots.
+    const long long active = n_ic - done_known;
+    const long long dead = (long long)s.A - active;
+    if (dead > 0 && dead * 8 >= (long long)s.A) {
+      e = launch_repack(p, s, cur, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints + 16, w.ints + 4, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) break;
+      s.A = w.h_ints[16];
+      cur ^= 1;
+      w.live ^= 1;
+      pending = -1;
+      if (s.A == 0) finished = true;
+    }
   }
-  if (e == cudaSuccess) e = launch_finish(p, s, xf, status, iters, nseg, capped ? 1 : 0, st);
+  if (e == cudaSuccess && capped) e = launch_abort(p, s, st);
   // aggregate: did any trajectory stop early?
-  if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_done, w.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints, w.ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (rounds_out) *rounds_out = rounds;
   if (e != cudaSuccess) return cuda_status(e);
-  if (capped || w.h_done[1] > 0) return PC_ENOTCONV;
+  if (capped || w.h_ints[1] > 0) return PC_ENOTCONV;
   return PC_OK;
 }
 
@@ -149,7 +179,7 @@ extern "C" pc_status pc_apply_operator(pc_plan *p, long long n_ic, const double 
   cudaStream_t st = (cudaStream_t)stream;
   Workspace &w = p->ws;
   const size_t ld = (size_t)w.ld, rows = (size_t)p->n * 6;
-  double *xs = w.ctl.x;
+  double *xs = w.ctl[w.live].x;
   cudaError_t e = cudaMemcpy2DAsync(xs, ld * 8, x0, (size_t)n_ic * 8, (size_t)n_ic * 8, 6, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(w.G, ld * 8, g, (size_t)n_ic * 8, (size_t)n_ic * 8, rows, cudaMemcpyDeviceToDevice, st);

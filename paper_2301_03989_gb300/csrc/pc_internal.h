@@ -29,7 +29,9 @@ struct Model {
   const double *coef; // [B][n_gr][3][deg+1]
 };
 
-// Per-trajectory control state, structure of arrays of length ld.
+// Per-trajectory control state, structure of arrays of length ld, indexed by
+// slot.  Active trajectories are packed into slots [0, A); ic[slot] is the
+// trajectory's index in the caller's arrays.
 struct Ctl {
   double *x;          // [6][ld] state at the start of the current segment
   double *hbase;      // base segment length
@@ -37,33 +39,47 @@ struct Ctl {
   double *e_best;
   unsigned long long *err;  // this round's max change, as non-negative double bits
   long long *p;       // segment start, in units of hbase / 2^max_depth
-  int *depth, *phase, *status, *sweeps, *seg_sweeps, *nstall, *nseg, *need_setup, *last;
+  int *depth, *phase, *status, *sweeps, *seg_sweeps, *nstall, *nseg, *need_setup, *last, *ic;
 };
+constexpr int kCtlDoubles = 13;  // x[6] + hbase, ta, tb, w1, w2, e_best, spare
+constexpr int kCtlInts = 10;
 
 // Sweep parameters of one call.
 struct Sweep {
   int N, n, kpad, rows_pad;  // degree, nodes, padded k extent, padded output rows (nodes 1..N)
   long long n_ic;
-  int ld;                    // leading dimension over trajectories (multiple of 8)
+  int ld;                    // leading dimension over slots (multiple of 8)
+  int A;                     // slots [0, A) may hold active trajectories
   double t0, tf, total, sgn;
   int segments, seg_mode, max_depth, max_iters, stall_sweeps, relative, warm;
   double tol, stall_factor, div_limit, trunc_tol;
   int max_ckpt;
   double *ckpt;              // [n_ic][max_ckpt][7] or nullptr
+  // outputs, indexed by trajectory, written when a trajectory finishes
+  double *xf;                // [6][n_ic]
+  int *status, *iters, *nseg;
+  // new-segment lists: setup of round r reads list (r & 1) and the control of
+  // round r appends to list ((r + 1) & 1)
+  int *list[2];
+  int *list_cnt;             // [2]
+  int list_cur;
 };
 
 struct Workspace {
-  long long cap = 0;         // trajectories the buffers hold
+  long long cap = 0;         // slots the buffers hold
   int ld = 0;
-  double *Y[2] = {nullptr, nullptr};  // [n][6][ld]
+  double *Y[2] = {nullptr, nullptr};  // [n][6][ld]; the other buffer receives a repack
   double *G = nullptr;       // [kpad][6][ld]; rows n..kpad-1 stay zero
-  double *E = nullptr;       // [n][B][3][ld] body positions at the nodes
-  double *Aind = nullptr;    // [n][3][ld] summed indirect acceleration at the nodes
-  Ctl ctl{};
-  void *ctl_block = nullptr; // single allocation behind ctl
-  int *done = nullptr;       // device counters [finished, stopped early]
-  int *h_done = nullptr;     // pinned host mirror, 2 slots of 2 ints
+  double *E[2] = {nullptr, nullptr};    // [n][B][3][ld] body positions at the nodes (+ repack target)
+  double *Aind[2] = {nullptr, nullptr}; // [n][3][ld] summed indirect acceleration (+ repack target)
+  Ctl ctl[2]{};              // live control state and repack target
+  void *ctl_block[2] = {nullptr, nullptr};
+  int *lists = nullptr;      // 2 x ld slot lists
+  int *ints = nullptr;       // [0..1] done counters [finished, stopped], [2..3] list counts, [4] repack count
+  int *pos = nullptr;        // [ld] repack destinations
+  int *h_ints = nullptr;     // pinned host mirror: 2 slots of 8 ints, [16] repack count
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  int live = 0;              // which of E/Aind/ctl is live
 };
 
 }  // namespace pcx
@@ -97,8 +113,12 @@ void free_workspace(pc_plan *plan);
 cudaError_t launch_init(const pc_plan *plan, const Sweep &s, const double *x0, cudaStream_t st);
 cudaError_t launch_round(const pc_plan *plan, const Sweep &s, int cur, cudaStream_t st,
                          cudaEvent_t *ev /* 5 events or nullptr */);
-cudaError_t launch_finish(const pc_plan *plan, const Sweep &s, double *xf, int *status, int *iters, int *nseg,
-                          int abort_rest, cudaStream_t st);
+// Moves the active slots of [0, s.A) to the front of the spare buffers (Y[cur]
+// -> Y[cur^1], E, Aind, control) and rebuilds list s.list_cur; the new count
+// lands in ints[4].  The caller then flips cur and ws.live.
+cudaError_t launch_repack(const pc_plan *plan, const Sweep &s, int cur, cudaStream_t st);
+// Trajectories still active after the round cap: flagged NOT_CONVERGED, outputs written.
+cudaError_t launch_abort(const pc_plan *plan, const Sweep &s, cudaStream_t st);
 cudaError_t launch_eval_ephemeris(const pc_plan *plan, long long n_pts, const double *t, double *rb, cudaStream_t st);
 cudaError_t launch_eval_dynamics(const pc_plan *plan, long long n_pts, const double *t, const double *y, double *f,
                                  cudaStream_t st);

@@ -169,34 +169,12 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
   return PC_OK;
 }
 
-pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
-  Workspace &w = p->ws;
-  if (n_ic <= w.cap && w.Y[0]) return PC_OK;
-  free_workspace(p);
-  const long long ld = (n_ic + 7) / 8 * 8;
-  if (ld > (1LL << 30)) return PC_EINVAL;
-  const size_t n = p->n, kpad = p->kpad, B = p->model.B;
-  cudaError_t e = cudaSuccess;
-  for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc(&w.Y[b], n * 6 * ld);
-  if (e == cudaSuccess) e = dalloc(&w.G, kpad * 6 * ld);
-  if (e == cudaSuccess) e = cudaMemset(w.G, 0, sizeof(double) * kpad * 6 * ld);
-  if (e == cudaSuccess && B > 0) e = dalloc(&w.E, n * B * 3 * ld);
-  if (e == cudaSuccess) e = dalloc(&w.Aind, n * 3 * ld);
-  if (e == cudaSuccess) e = cudaMemset(w.Aind, 0, sizeof(double) * n * 3 * ld);
-  // control block: 6 + 7 doubles, 1 u64, 1 i64 and 9 ints per trajectory
-  const size_t bytes = (size_t)ld * (13 * 8 + 8 + 8 + 9 * 4) + 256;
-  if (e == cudaSuccess) e = cudaMalloc(&w.ctl_block, bytes);
-  if (e == cudaSuccess) e = cudaMemset(w.ctl_block, 0, bytes);
-  if (e == cudaSuccess) e = dalloc(&w.done, 2);  // [finished, stopped early]
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&w.h_done, sizeof(int) * 4);
-  for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    free_workspace(p);
-    return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
-  }
-  char *c = (char *)w.ctl_block;
+namespace {
+// Carves one control block (kCtlDoubles doubles, one u64, one i64 and kCtlInts
+// ints per slot) into the Ctl arrays.
+void carve_ctl(void *block, long long ld, Ctl &t) {
+  char *c = (char *)block;
   auto take = [&](size_t each) { char *r = c; c += each * ld; return r; };
-  Ctl &t = w.ctl;
   t.x = (double *)take(8 * 6);
   t.hbase = (double *)take(8);
   t.ta = (double *)take(8);
@@ -204,7 +182,7 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
   t.w1 = (double *)take(8);
   t.w2 = (double *)take(8);
   t.e_best = (double *)take(8);
-  take(8);  // spare double column (keeps the layout at 13 doubles)
+  take(8);  // spare double column
   t.err = (unsigned long long *)take(8);
   t.p = (long long *)take(8);
   t.depth = (int *)take(4);
@@ -216,21 +194,59 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
   t.nseg = (int *)take(4);
   t.need_setup = (int *)take(4);
   t.last = (int *)take(4);
+  t.ic = (int *)take(4);
+}
+}  // namespace
+
+pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
+  Workspace &w = p->ws;
+  if (n_ic <= w.cap && w.Y[0]) return PC_OK;
+  free_workspace(p);
+  const long long ld = (n_ic + 7) / 8 * 8;
+  if (ld > (1LL << 30)) return PC_EINVAL;
+  const size_t n = p->n, kpad = p->kpad, B = p->model.B;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc(&w.Y[b], n * 6 * ld);
+  if (e == cudaSuccess) e = dalloc(&w.G, kpad * 6 * ld);
+  if (e == cudaSuccess) e = cudaMemset(w.G, 0, sizeof(double) * kpad * 6 * ld);
+  const size_t ctl_bytes = (size_t)ld * (kCtlDoubles * 8 + 8 + 8 + kCtlInts * 4) + 256;
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+    if (B > 0) e = dalloc(&w.E[b], n * B * 3 * ld);
+    if (e == cudaSuccess) e = dalloc(&w.Aind[b], n * 3 * ld);
+    if (e == cudaSuccess) e = cudaMemset(w.Aind[b], 0, sizeof(double) * n * 3 * ld);
+    if (e == cudaSuccess) e = cudaMalloc(&w.ctl_block[b], ctl_bytes);
+    if (e == cudaSuccess) e = cudaMemset(w.ctl_block[b], 0, ctl_bytes);
+  }
+  if (e == cudaSuccess) e = dalloc(&w.lists, 2 * ld);
+  if (e == cudaSuccess) e = dalloc(&w.pos, ld);
+  if (e == cudaSuccess) e = dalloc(&w.ints, 8);
+  if (e == cudaSuccess) e = cudaMemset(w.ints, 0, sizeof(int) * 8);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&w.h_ints, sizeof(int) * 24);
+  for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_workspace(p);
+    return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
+  }
+  for (int b = 0; b < 2; b++) carve_ctl(w.ctl_block[b], ld, w.ctl[b]);
   w.cap = ld;
   w.ld = (int)ld;
+  w.live = 0;
   return PC_OK;
 }
 
 void pcx::free_workspace(pc_plan *p) {
   Workspace &w = p->ws;
-  cudaFree(w.Y[0]);
-  cudaFree(w.Y[1]);
+  for (int b = 0; b < 2; b++) {
+    cudaFree(w.Y[b]);
+    cudaFree(w.E[b]);
+    cudaFree(w.Aind[b]);
+    cudaFree(w.ctl_block[b]);
+  }
   cudaFree(w.G);
-  cudaFree(w.E);
-  cudaFree(w.Aind);
-  cudaFree(w.ctl_block);
-  cudaFree(w.done);
-  if (w.h_done) cudaFreeHost(w.h_done);
+  cudaFree(w.lists);
+  cudaFree(w.pos);
+  cudaFree(w.ints);
+  if (w.h_ints) cudaFreeHost(w.h_ints);
   for (int i = 0; i < 2; i++)
     if (w.ev[i]) cudaEventDestroy(w.ev[i]);
   w = Workspace();

@@ -43,7 +43,7 @@ __device__ __forceinline__ unsigned long long err_bits(double e) {
 // multiply-add) so every trajectory's segment bounds and node times are the
 // exactly rounded values of these formulas.
 // ---------------------------------------------------------------------------
-__device__ void schedule(const Sweep &s, Ctl &c, int m) {
+__device__ void schedule(const Sweep &s, Ctl &c, int m, int list_next) {
   const int D = s.max_depth;
   const double u = scalbn(c.hbase[m], -D);
   const long long L = 1LL << (D - c.depth[m]);
@@ -66,6 +66,17 @@ __device__ void schedule(const Sweep &s, Ctl &c, int m) {
   c.seg_sweeps[m] = 0;
   c.nstall[m] = 0;
   c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);  // +inf
+  const int k = atomicAdd(s.list_cnt + list_next, 1);
+  s.list[list_next][k] = m;
+}
+
+// Final outputs of a trajectory, written when it finishes.
+__device__ __forceinline__ void write_outputs(const Sweep &s, const Ctl &c, int m) {
+  const long long i = c.ic[m];
+  for (int q = 0; q < 6; q++) s.xf[q * s.n_ic + i] = c.x[q * s.ld + m];
+  if (s.status) s.status[i] = c.status[m];
+  if (s.iters) s.iters[i] = c.sweeps[m];
+  if (s.nseg) s.nseg[i] = c.nseg[m];
 }
 
 __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, int *done) {
@@ -90,6 +101,7 @@ __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, 
       h = dmul(twopi, sqrt(dmul(dmul(a, a), a) / md.mu_c)) / (double)s.segments;
     }
   }
+  c.ic[m] = (int)m;
   c.hbase[m] = h;
   c.p[m] = 0;
   c.depth[m] = 0;
@@ -100,12 +112,13 @@ __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, 
   c.need_setup[m] = 0;
   if (!finite || !(s.total > 0.0)) {
     c.phase[m] = PH_DONE;
+    write_outputs(s, c, (int)m);
     atomicAdd(done, 1);
     if (!finite) atomicAdd(done + 1, 1);
     return;
   }
   c.phase[m] = PH_ITER;
-  schedule(s, c, (int)m);
+  schedule(s, c, (int)m, s.list_cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -196,28 +209,36 @@ __device__ __forceinline__ void add_indirect(const Model &md, int b, const doubl
 }
 
 // New segments: node times, body positions and summed indirect term at the
-// nodes, warm start.  Grid: x over trajectories, y over nodes.
+// nodes, warm start -- only for the slots on this round's new-segment list
+// (grid-stride over list entries x nodes, entries fastest).  Also clears the
+// list the control kernel of this round will fill.
 __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau, double *__restrict__ Y,
                         double *__restrict__ E, double *__restrict__ Aind) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (m >= s.n_ic) return;
-  if (c.phase[m] != PH_ITER || !c.need_setup[m]) return;
+  const int cur = s.list_cur;
+  if (blockIdx.x == 0 && threadIdx.x == 0) s.list_cnt[cur ^ 1] = 0;
+  const long long count = s.list_cnt[cur];
+  const int *__restrict__ list = s.list[cur];
+  const long long total = count * s.n;
   const int ld = s.ld, B = md.B;
-  const double t = dadd(c.w1[m], dmul(c.w2[m], tau[j]));
-  double ind[3] = {0.0, 0.0, 0.0};
-  for (int b = 0; b < B; b++) {
-    double r[3];
-    ephem_at(md, t, b, r);
-    for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
-    if (md.indirect) add_indirect(md, b, r, ind);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / count);
+    const int m = list[i - (long long)j * count];
+    const double t = dadd(c.w1[m], dmul(c.w2[m], tau[j]));
+    double ind[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < B; b++) {
+      double r[3];
+      ephem_at(md, t, b, r);
+      for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
+      if (md.indirect) add_indirect(md, b, r, ind);
+    }
+    for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
+    double x0[6], y[6];
+    for (int q = 0; q < 6; q++) x0[q] = c.x[q * ld + m];
+    bool ok = false;
+    if (j > 0 && s.warm) ok = kepler_dt(md.mu_c, x0, dsub(t, c.ta[m]), y);
+    for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = ok ? y[q] : x0[q];
   }
-  for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
-  double x0[6], y[6];
-  for (int q = 0; q < 6; q++) x0[q] = c.x[q * ld + m];
-  bool ok = false;
-  if (j > 0 && s.warm) ok = kepler_dt(md.mu_c, x0, dsub(t, c.ta[m]), y);
-  for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = ok ? y[q] : x0[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -255,7 +276,7 @@ __global__ void k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y, 
                         const double *__restrict__ Aind, double *__restrict__ G) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
-  if (m >= s.n_ic || c.phase[m] != PH_ITER) return;
+  if (m >= s.A || c.phase[m] != PH_ITER) return;
   const int ld = s.ld;
   const double w2 = c.w2[m];
   const size_t yb = (size_t)j * 6 * ld + m;
@@ -298,13 +319,14 @@ __global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *
   const int rt = warp % n_rt;
   const int ct = warp / n_rt;
   const int m0 = ct * 8;
-  if (m0 >= s.ld) return;
+  const int ncols = DIAG ? (int)s.n_ic : s.A;
+  if (m0 >= ncols) return;
   const int g = lane >> 2, t = lane & 3;
   const int ld = s.ld;
   bool mine_active = false;
   if (!DIAG) {
     const int mm = m0 + g;
-    mine_active = (mm < s.n_ic) && c.phase[mm] == PH_ITER;
+    mine_active = (mm < ncols) && c.phase[mm] == PH_ITER;
     if (!__any_sync(0xffffffffu, mine_active)) return;
   }
   double acc[6][4];
@@ -330,7 +352,7 @@ __global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *
 #pragma unroll
     for (int e = 0; e < 2; e++) {        // column 2t+e
       const int m = m0 + 2 * t + e;
-      if (j > s.N || m >= s.n_ic) continue;
+      if (j > s.N || m >= ncols) continue;
       if (!DIAG && c.phase[m] != PH_ITER) continue;
       double yn[6];
       const size_t base = (size_t)j * 6 * ld + m;
@@ -360,7 +382,7 @@ __global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *
 #pragma unroll
     for (int e = 0; e < 2; e++) {
       const int m = m0 + 2 * t + e;
-      if (m < s.n_ic && (DIAG || c.phase[m] == PH_ITER))
+      if (m < ncols && (DIAG || c.phase[m] == PH_ITER))
 #pragma unroll
         for (int q = 0; q < 6; q++) Ynew[(size_t)q * ld + m] = c.x[q * ld + m];
     }
@@ -373,7 +395,7 @@ __global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *
       v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 8));
       v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 16));
       const int m = m0 + 2 * t + e;
-      if (g == 0 && m < s.n_ic && c.phase[m] == PH_ITER) atomicMax(c.err + m, err_bits(v));
+      if (g == 0 && m < ncols && c.phase[m] == PH_ITER) atomicMax(c.err + m, err_bits(v));
     }
   }
 }
@@ -388,12 +410,14 @@ __global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *
 // Position components are measured against max_j |r_j|, velocity ones against
 // max_j |v_j| (relative mode).
 // ---------------------------------------------------------------------------
-__device__ double tail_estimate(const Sweep &s, const double *__restrict__ tau, const double *__restrict__ G,
-                                const double *__restrict__ Y, int m) {
-  const int ld = s.ld, N = s.N;
+// Warp-cooperative: lanes split the nodes of slot m, the sums are reduced
+// across the warp and every lane returns the estimate.
+__device__ double warp_tail_estimate(const Sweep &s, const double *__restrict__ tau, const double *__restrict__ G,
+                                     const double *__restrict__ Y, int m) {
+  const int ld = s.ld, N = s.N, lane = threadIdx.x & 31;
   double sN[6] = {0, 0, 0, 0, 0, 0}, sN1[6] = {0, 0, 0, 0, 0, 0};
   double rmax = 0.0, vmax = 0.0;
-  for (int j = 0; j <= N; j++) {
+  for (int j = lane; j <= N; j += 32) {
     const double w = (j == 0 || j == N) ? 0.5 : 1.0;
     const double sg = ((N + j) & 1) ? -w : w;
     const double tj = tau[j] * sg;
@@ -411,6 +435,16 @@ __device__ double tail_estimate(const Sweep &s, const double *__restrict__ tau, 
       vmax = fmax(vmax, sqrt(y3 * y3 + y4 * y4 + y5 * y5));
     }
   }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      sN[q] += __shfl_xor_sync(0xffffffffu, sN[q], o);
+      sN1[q] += __shfl_xor_sync(0xffffffffu, sN1[q], o);
+    }
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  }
   double er = 0.0, ev = 0.0;
 #pragma unroll
   for (int q = 0; q < 6; q++) {
@@ -426,38 +460,52 @@ __device__ double tail_estimate(const Sweep &s, const double *__restrict__ tau, 
 
 // Per-trajectory decisions after a sweep.  Same rules, same order as the
 // oracle: blow-up, tolerance, stall, cap; then the resolution test on an
-// accepted segment; accept (advance, grow one level) or fail (halve).
+// accepted segment; accept (advance, grow one level) or fail (halve).  A
+// finished trajectory writes its outputs.  The block size is a multiple of 32
+// and every lane reaches the warp-cooperative resolution test.
 __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const double *__restrict__ G,
                           const double *__restrict__ Ynew, int *done) {
-  const long long mm = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (mm >= s.n_ic) return;
-  const int m = (int)mm;
-  if (c.phase[m] != PH_ITER) return;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = m < s.A && c.phase[m] == PH_ITER;
   const int ld = s.ld;
-  c.need_setup[m] = 0;
-  const double e = __longlong_as_double((long long)c.err[m]);
-  c.err[m] = 0ULL;
-  const int ss = ++c.seg_sweeps[m];
-  c.sweeps[m] += 1;
   int out = SEG_CONTINUE;
-  if (!(e <= s.div_limit)) {
-    out = SEG_FAIL_DIV;
-  } else if (e < s.tol) {
-    out = SEG_OK;
-  } else {
-    if (e < c.e_best[m]) {
-      c.e_best[m] = e;
-      c.nstall[m] = 0;
+  int ss = 0;
+  if (act) {
+    c.need_setup[m] = 0;
+    const double e = __longlong_as_double((long long)c.err[m]);
+    c.err[m] = 0ULL;
+    ss = ++c.seg_sweeps[m];
+    c.sweeps[m] += 1;
+    if (!(e <= s.div_limit)) {
+      out = SEG_FAIL_DIV;
+    } else if (e < s.tol) {
+      out = SEG_OK;
     } else {
-      c.nstall[m] += 1;
+      if (e < c.e_best[m]) {
+        c.e_best[m] = e;
+        c.nstall[m] = 0;
+      } else {
+        c.nstall[m] += 1;
+      }
+      if (c.nstall[m] >= s.stall_sweeps && c.e_best[m] < s.stall_factor * s.tol) out = SEG_STALLED;
+      else if (ss >= s.max_iters) out = SEG_FAIL_CAP;
     }
-    if (c.nstall[m] >= s.stall_sweeps && c.e_best[m] < s.stall_factor * s.tol) out = SEG_STALLED;
-    else if (ss >= s.max_iters) out = SEG_FAIL_CAP;
   }
-  if (out == SEG_CONTINUE) return;
-  if ((out == SEG_OK || out == SEG_STALLED) && s.trunc_tol > 0.0 && tail_estimate(s, tau, G, Ynew, m) > s.trunc_tol)
-    out = SEG_FAIL_TRUNC;
+  const bool want_tail = act && (out == SEG_OK || out == SEG_STALLED) && s.trunc_tol > 0.0;
+  unsigned pending = __ballot_sync(0xffffffffu, want_tail);
+  double my_tail = 0.0;
+  while (pending) {
+    const int b = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const int mb = __shfl_sync(0xffffffffu, m, b);
+    const double tl = warp_tail_estimate(s, tau, G, Ynew, mb);
+    if (lane == b) my_tail = tl;
+  }
+  if (!act || out == SEG_CONTINUE) return;
+  if (want_tail && !(my_tail <= s.trunc_tol)) out = SEG_FAIL_TRUNC;
   const int D = s.max_depth;
+  const int list_next = s.list_cur ^ 1;
   bool accept = (out == SEG_OK || out == SEG_STALLED);
   if (out == SEG_FAIL_TRUNC && c.depth[m] >= D) {
     accept = true;
@@ -467,7 +515,7 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const 
     if (out == SEG_STALLED) c.status[m] |= PC_IC_STALLED;
     const int k = c.nseg[m];
     if (s.ckpt && k < s.max_ckpt) {
-      double *ck = s.ckpt + ((size_t)m * s.max_ckpt + k) * 7;
+      double *ck = s.ckpt + ((size_t)c.ic[m] * s.max_ckpt + k) * 7;
       ck[0] = c.ta[m];
       for (int q = 0; q < 6; q++) ck[1 + q] = c.x[q * ld + m];
     }
@@ -477,36 +525,89 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const 
     c.p[m] += 1LL << (D - c.depth[m]);
     if (c.last[m]) {
       c.phase[m] = PH_DONE;
+      write_outputs(s, c, m);
       atomicAdd(done, 1);
       return;
     }
     if (c.depth[m] > 0) c.depth[m] -= 1;
-    schedule(s, c, m);
+    schedule(s, c, m, list_next);
   } else {
     c.depth[m] += 1;
     if (c.depth[m] > D) {
       c.status[m] |= (out == SEG_FAIL_DIV) ? PC_IC_NONFINITE : PC_IC_NOT_CONVERGED;
       c.phase[m] = PH_DONE;
+      write_outputs(s, c, m);
       atomicAdd(done, 1);
       atomicAdd(done + 1, 1);
       return;
     }
-    schedule(s, c, m);
+    schedule(s, c, m, list_next);
   }
 }
 
-__global__ void k_finish(Sweep s, Ctl c, double *__restrict__ xf, int *__restrict__ status, int *__restrict__ iters,
-                         int *__restrict__ nseg, int abort_rest) {
-  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= s.n_ic) return;
-  if (abort_rest && c.phase[m] != PH_DONE) {
-    c.status[m] |= PC_IC_NOT_CONVERGED;
-    c.phase[m] = PH_DONE;
+// ---- repack: move active slots to the front of the spare buffers ------------
+__global__ void k_repack_pos(int A, const int *__restrict__ phase, int *__restrict__ pos, int *counter) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool alive = m < A && phase[m] == PH_ITER;
+  const unsigned mask = __ballot_sync(0xffffffffu, alive);
+  int base = 0;
+  if (mask) {
+    const int leader = __ffs(mask) - 1;
+    if (lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
   }
-  for (int q = 0; q < 6; q++) xf[q * s.n_ic + m] = c.x[q * s.ld + m];
-  if (status) status[m] = c.status[m];
-  if (iters) iters[m] = c.sweeps[m];
-  if (nseg) nseg[m] = c.nseg[m];
+  if (m < A) pos[m] = alive ? base + __popc(mask & ((1u << lane) - 1u)) : -1;
+}
+
+// Copies rows [0, rows) of a [rows][ld] array for every slot that moves.
+__global__ void k_repack_rows(int A, int ld, long long rows, const int *__restrict__ pos,
+                              const double *__restrict__ src, double *__restrict__ dst) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= A) return;
+  const int d = pos[m];
+  if (d < 0) return;
+  for (long long r = blockIdx.y; r < rows; r += gridDim.y) dst[(size_t)r * ld + d] = src[(size_t)r * ld + m];
+}
+
+__global__ void k_repack_ctl(Sweep s, Ctl a, Ctl b, const int *__restrict__ pos) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= s.A) return;
+  const int d = pos[m];
+  if (d < 0) return;
+  const int ld = s.ld;
+  for (int q = 0; q < 6; q++) b.x[q * ld + d] = a.x[q * ld + m];
+  b.hbase[d] = a.hbase[m];
+  b.ta[d] = a.ta[m];
+  b.tb[d] = a.tb[m];
+  b.w1[d] = a.w1[m];
+  b.w2[d] = a.w2[m];
+  b.e_best[d] = a.e_best[m];
+  b.err[d] = a.err[m];
+  b.p[d] = a.p[m];
+  b.depth[d] = a.depth[m];
+  b.phase[d] = a.phase[m];
+  b.status[d] = a.status[m];
+  b.sweeps[d] = a.sweeps[m];
+  b.seg_sweeps[d] = a.seg_sweeps[m];
+  b.nstall[d] = a.nstall[m];
+  b.nseg[d] = a.nseg[m];
+  b.need_setup[d] = a.need_setup[m];
+  b.last[d] = a.last[m];
+  b.ic[d] = a.ic[m];
+  if (a.need_setup[m]) {
+    const int k = atomicAdd(s.list_cnt + s.list_cur, 1);
+    s.list[s.list_cur][k] = d;
+  }
+}
+
+// Round cap reached: remaining trajectories stop with NOT_CONVERGED.
+__global__ void k_abort(Sweep s, Ctl c) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= s.A || c.phase[m] != PH_ITER) return;
+  c.status[m] |= PC_IC_NOT_CONVERGED;
+  c.phase[m] = PH_DONE;
+  write_outputs(s, c, m);
 }
 
 // ---- kernel-level diagnostics ------------------------------------------------
@@ -558,32 +659,52 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 // ---- launchers ----------------------------------------------------------------
 cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cudaStream_t st) {
   const Workspace &w = p->ws;
-  cudaError_t e = cudaMemsetAsync(w.done, 0, 2 * sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(w.ints, 0, 8 * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_init<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, w.ctl, p->model, x0, w.done);
+  k_init<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, w.ctl[w.live], p->model, x0, w.ints);
   return cudaGetLastError();
 }
 
 cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t st, cudaEvent_t *ev) {
   const Workspace &w = p->ws;
+  if (s.A <= 0) return cudaSuccess;
+  const Ctl &c = w.ctl[w.live];
   double *Yc = w.Y[cur], *Yn = w.Y[cur ^ 1];
-  const dim3 gnode(blocks_for(s.n_ic, kThreads), s.n);
+  double *E = w.E[w.live], *Ai = w.Aind[w.live];
   if (ev) cudaEventRecord(ev[0], st);
-  k_setup<<<gnode, kThreads, 0, st>>>(s, w.ctl, p->model, p->d_tau, Yc, w.E, w.Aind);
+  k_setup<<<152 * 4, kThreads, 0, st>>>(s, c, p->model, p->d_tau, Yc, E, Ai);
   if (ev) cudaEventRecord(ev[1], st);
-  k_force<<<gnode, kThreads, 0, st>>>(s, w.ctl, p->model, Yc, w.E, w.Aind, w.G);
+  const dim3 gnode(blocks_for(s.A, kThreads), s.n);
+  k_force<<<gnode, kThreads, 0, st>>>(s, c, p->model, Yc, E, Ai, w.G);
   if (ev) cudaEventRecord(ev[2], st);
-  const long long warps = (long long)(s.rows_pad / 16) * (s.ld / 8);
-  k_contract<false><<<blocks_for(warps * 32, 256), 256, 0, st>>>(s, w.ctl, p->d_K, w.G, Yc, Yn);
+  const long long warps = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
+  k_contract<false><<<blocks_for(warps * 32, 256), 256, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn);
   if (ev) cudaEventRecord(ev[3], st);
-  k_control<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, w.ctl, p->d_tau, w.G, Yn, w.done);
+  k_control<<<blocks_for(s.A, kThreads), kThreads, 0, st>>>(s, c, p->d_tau, w.G, Yn, w.ints);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const pc_plan *p, const Sweep &s, double *xf, int *status, int *iters, int *nseg,
-                          int abort_rest, cudaStream_t st) {
-  k_finish<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, p->ws.ctl, xf, status, iters, nseg, abort_rest);
+cudaError_t launch_repack(const pc_plan *p, const Sweep &s, int cur, cudaStream_t st) {
+  const Workspace &w = p->ws;
+  if (s.A <= 0) return cudaSuccess;
+  const int a = w.live, b = w.live ^ 1;
+  cudaError_t e = cudaMemsetAsync(w.ints + 4, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.list_cnt + s.list_cur, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = blocks_for(s.A, kThreads);
+  k_repack_pos<<<nb, kThreads, 0, st>>>(s.A, w.ctl[a].phase, w.pos, w.ints + 4);
+  const long long n = p->n, B = p->model.B;
+  k_repack_rows<<<dim3(nb, 64), kThreads, 0, st>>>(s.A, s.ld, n * 6, w.pos, w.Y[cur], w.Y[cur ^ 1]);
+  if (B > 0) k_repack_rows<<<dim3(nb, 64), kThreads, 0, st>>>(s.A, s.ld, n * B * 3, w.pos, w.E[a], w.E[b]);
+  k_repack_rows<<<dim3(nb, 64), kThreads, 0, st>>>(s.A, s.ld, n * 3, w.pos, w.Aind[a], w.Aind[b]);
+  k_repack_ctl<<<nb, kThreads, 0, st>>>(s, w.ctl[a], w.ctl[b], w.pos);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_abort(const pc_plan *p, const Sweep &s, cudaStream_t st) {
+  if (s.A <= 0) return cudaSuccess;
+  k_abort<<<blocks_for(s.A, kThreads), kThreads, 0, st>>>(s, p->ws.ctl[p->ws.live]);
   return cudaGetLastError();
 }
 
@@ -616,7 +737,7 @@ cudaError_t launch_apply_operator(const pc_plan *p, long long n_ic, int ld, cons
   s.rows_pad = p->rows_pad;
   s.n_ic = n_ic;
   s.ld = ld;
-  Ctl c = w.ctl;
+  Ctl c = w.ctl[w.live];
   c.x = const_cast<double *>(x0);
   const long long warps = (long long)(s.rows_pad / 16) * (s.ld / 8);
   k_contract<true><<<blocks_for(warps * 32, 256), 256, 0, st>>>(s, c, p->d_K, G, nullptr, Y);

@@ -187,3 +187,20 @@ def test_edge_cases(pc, ora):
     assert pc.lib().pc_propagate(plan.handle, 4, None, 0.0, 1.0, 0.0, None, None, None, None) == pc.PC_EINVAL
     assert pc.lib().pc_propagate(plan.handle, 0, None, 0.0, 1.0, 0.0, None, None, None, None) == pc.PC_OK
     plan.close()
+
+
+def test_repack_keeps_results_bitwise(pc):
+    """Half the batch finishes at once (non-finite inputs), which triggers the
+    compaction of active trajectories into the front slots; the survivors'
+    results are bitwise those of a batch without the dead half."""
+    w = W.config2(M=64)
+    tf = 30 * W.DAY
+    x = w.x0.copy()
+    x[::2, 1] = np.nan
+    g = run_gpu(pc, w, x, tf=tf, max_ckpt=64)
+    ref = run_gpu(pc, w, w.x0[1::2], tf=tf, max_ckpt=64)
+    assert (g["status"][::2] == pc.PC_IC_NONFINITE).all()
+    np.testing.assert_array_equal(g["xf"][1::2], ref["xf"])
+    np.testing.assert_array_equal(g["iters"][1::2], ref["iters"])
+    np.testing.assert_array_equal(g["nseg"][1::2], ref["nseg"])
+    np.testing.assert_array_equal(g["ckpt"][1::2], ref["ckpt"])
