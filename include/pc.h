@@ -174,6 +174,28 @@ pc_status pc_eval_warm_start(pc_plan *plan, long long n_pts, const double *x0, c
 pc_status pc_apply_operator(pc_plan *plan, long long n_ic, const double *x0, const double *g, double *y,
                             void *stream);
 
+/* Allocation-free variant of pc_apply_operator (the paper has no counterpart:
+ * it is an addition of this library for callers that cannot allocate device
+ * memory at call time -- for example a caller whose GPU memory is owned by
+ * another allocator with a fixed budget, or a latency-sensitive caller that
+ * must not risk the implicit device synchronisation of cudaMalloc/cudaFree).
+ * Same arguments and result as pc_apply_operator, but the operands are staged
+ * in a fixed 32 MiB device array that is part of the library image (every GPU
+ * that loads the library holds it until the process exits) instead of the
+ * plan's workspace; the call makes no cudaMalloc, cudaFree or other allocating
+ * call.
+ *   Limit: (4*ceil((N+1)/4) + N + 2) * 6 * 8 * ceil(n_ic/8)*8 bytes must fit in
+ *   32 MiB (N = 128: up to 2,664 trajectories); larger n_ic returns PC_EINVAL.
+ *   The plan must belong to the current device (else PC_EINVAL).
+ *   The first call on a device looks up the array's device address (a one-time
+ *   set-up per device, with that device current); make that first call before
+ *   any stream capture.
+ *   All calls share the one array and it keeps the last call's contents: calls
+ *   whose work overlaps on the GPU (different streams, or different host
+ *   threads) race on it and must be serialised by the caller. */
+pc_status pc_apply_operator_static(pc_plan *plan, long long n_ic, const double *x0, const double *g, double *y,
+                                   void *stream);
+
 /* ---- Per-kernel timing ----------------------------------------------------
  * With profiling on, pc_propagate / pc_propagate_ex record a CUDA event
  * between consecutive kernels of every sweep round on the call's stream; the

@@ -24,7 +24,7 @@ PC_PREC_FP64, PC_PREC_MIXED = 0, 1
 
 EXPORTS = ["pc_options_default", "pc_plan_create", "pc_propagate", "pc_propagate_ex", "pc_eval_ephemeris",
            "pc_eval_dynamics", "pc_eval_warm_start", "pc_apply_operator", "pc_plan_operator", "pc_plan_destroy",
-           "pc_status_string", "pc_plan_set_profiling", "pc_plan_kernel_times"]
+           "pc_status_string", "pc_plan_set_profiling", "pc_plan_kernel_times", "pc_apply_operator_static"]
 KERNEL_NAMES = ["setup", "force", "contract", "control"]
 
 
@@ -73,6 +73,7 @@ def lib():
             L.pc_eval_dynamics.argtypes = [vp, ll, vp, vp, vp, vp]
             L.pc_eval_warm_start.argtypes = [vp, ll, vp, vp, vp, vp]
             L.pc_apply_operator.argtypes = [vp, ll, vp, vp, vp, vp]
+            L.pc_apply_operator_static.argtypes = [vp, ll, vp, vp, vp, vp]
             L.pc_plan_operator.argtypes = [vp, vp, vp]
             L.pc_plan_destroy.argtypes = [vp]
             L.pc_plan_destroy.restype = None
@@ -209,6 +210,12 @@ def eval_warm_start(plan: Plan, x0, dt, x, stream=None):
 def apply_operator(plan: Plan, x0, g, y, stream=None):
     _check(lib().pc_apply_operator(plan.handle, int(x0.shape[-1]), _ptr(x0), _ptr(g), _ptr(y), _stream(stream)),
            "pc_apply_operator")
+
+
+def apply_operator_static(plan: Plan, x0, g, y, stream=None):
+    """pc_apply_operator through the library's fixed device array (no allocation)."""
+    _check(lib().pc_apply_operator_static(plan.handle, int(x0.shape[-1]), _ptr(x0), _ptr(g), _ptr(y),
+                                          _stream(stream)), "pc_apply_operator_static")
 
 
 def plan_operator(plan: Plan):
