@@ -16,6 +16,11 @@ initial states copied from pinned host memory and the final states + status
 copied back inside the timed region.  --impl reference times the CPU oracle
 on a bounded sample of the same workload on the host cores.
 
+The headline path is the mixed-precision batched sweep (FP32 sweeps on the
+deviation from the Keplerian warm start, then FP64 refinement to 1e-13); the
+plain FP64 GPU sweep runs on the same inputs and is reported beside it
+(stats.plain_fp64), with the difference between the two results.
+
 With N > 1 (torchrun) each rank propagates its own 4096 trajectories (weak
 scaling, no data-path collective); rank 0 prints the max-over-ranks time.
 """
@@ -39,10 +44,9 @@ METRIC = "trajectories/s (N-body, <=1e-10 rel err): mixed+batched vs plain FP64 
 UNIT = "trajectories/s"
 IC_PER_RANK = 4096
 
-# Per-launch DRAM bytes (read + write) of the dominant kernel from an ncu
-# capture of the same kernel and workload (profiles/contract_cfg2_ncu.txt);
-# None until a capture of the current kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of the FP64 contraction per trajectory-sweep from an
+# ncu capture of the current kernel (profiles/); None until one exists.
+TRAFFIC_BYTES_PER_SWEEP = None
 
 
 def _peaks():
@@ -198,6 +202,36 @@ def contract_flops_per_sweep(N: int) -> float:
     return 2.0 * N * (N + 1) * 6
 
 
+def timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, steps, dev):
+    """Runs `steps` propagations (L2 flushed before each), CUDA events on the
+    launch stream around each; returns per-step ms, rounds and kernel times."""
+    import torch
+    pc.set_profiling(plan, True)
+    pc.kernel_times(plan)                       # clear
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    rounds = 0
+    torch.cuda.synchronize(dev)
+    for k in range(steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        _, r = pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, iters=it, stream=stream)
+        rounds += r
+        ev1[k].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    kt = pc.kernel_times(plan)
+    pc.set_profiling(plan, False)
+    return ms, rounds, kt
+
+
+def rel_errors(a, b):
+    """Per-trajectory relative position / velocity differences of planar [6][M] arrays."""
+    er = np.linalg.norm(a[:3] - b[:3], axis=0) / np.linalg.norm(b[:3], axis=0)
+    ev = np.linalg.norm(a[3:] - b[3:], axis=0) / np.linalg.norm(b[3:], axis=0)
+    return er, ev
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2301_03989_gb300 import build as B
@@ -214,7 +248,9 @@ def run_ours(args, world, rank, local):
     lo, hi = shard(wall.n_ic, world, rank)
     w = wall.subset(np.arange(lo, hi))
     M = w.n_ic
-    plan = pc.plan_from_workload(w)
+    mixed = args.precision == "mixed"
+    plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED if mixed else pc.PC_PREC_FP64,
+                                 switch_tol=args.switch_tol)
     stream = torch.cuda.Stream(device=dev)
     x0 = torch.as_tensor(W.to_planar(w.x0), device=dev)
     xf = torch.zeros_like(x0)
@@ -222,37 +258,19 @@ def run_ours(args, world, rank, local):
     it = torch.zeros(M, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
 
-    def step():
-        code, rounds = pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, iters=it, stream=stream)
-        return rounds
-
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step()
+            pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, iters=it, stream=stream)
         torch.cuda.synchronize(dev)
         if world > 1:
             torch.distributed.barrier()
-        pc.set_profiling(plan, True)
-        pc.kernel_times(plan)                       # clear
         clocks = ClockSampler(local)
         clocks.start()
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        rounds_total = 0
-        torch.cuda.synchronize(dev)
-        for k in range(args.steps):
-            flush.zero_()
-            ev0[k].record(stream)
-            rounds_total += step()
-            ev1[k].record(stream)
-        torch.cuda.synchronize(dev)
+        step_ms, rounds_total, ktimes = timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, args.steps, dev)
         if world > 1:
             torch.distributed.barrier()
         clk = clocks.stop()
-        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-        ktimes = pc.kernel_times(plan)
-        pc.set_profiling(plan, False)
-        iters = it.cpu().numpy().astype(np.int64)
+        xf_main = xf.clone()
         status = st.cpu().numpy()
 
         # end to end through the C ABI with host buffers
@@ -267,12 +285,27 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize(dev)
             a.record(stream)
             x0.copy_(hx0, non_blocking=True)
-            step()
+            pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, iters=it, stream=stream)
             hxf.copy_(xf, non_blocking=True)
             hst.copy_(st, non_blocking=True)
             b.record(stream)
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
+
+        # the plain FP64 GPU sweep on the same inputs (the metric's comparator)
+        plain = None
+        if mixed and not args.no_plain:
+            plan64 = pc.plan_from_workload(w, precision=pc.PC_PREC_FP64)
+            xf64 = torch.zeros_like(x0)
+            st64 = torch.zeros_like(st)
+            it64 = torch.zeros_like(it)
+            for _ in range(1):
+                pc.propagate(plan64, x0, w.t0, w.tf, xf64, status=st64, iters=it64, stream=stream)
+            ms64, rounds64, kt64 = timed_steps(pc, plan64, w, x0, xf64, st64, it64, stream, flush,
+                                               args.plain_steps, dev)
+            er, ev = rel_errors(xf_main.cpu().numpy(), xf64.cpu().numpy())
+            plain = dict(ms=sum(ms64) / len(ms64), kt=kt64, rounds=rounds64 / len(ms64), er=er, ev=ev)
+            plan64.close()
 
     ms = sum(step_ms) / len(step_ms)
     ms_max = max_over_ranks(ms, world, dev)
@@ -282,19 +315,22 @@ def run_ours(args, world, rank, local):
     value = total_ic / (ms_max / 1000.0)
     e2e_value = total_ic / (e2e_max / 1000.0)
 
-    # roofline of the dominant kernel (the FP64 tensor-core contraction)
-    kname = max(ktimes, key=lambda k: ktimes[k][1])
+    # roofline of the FP64 tensor-core contraction (the dominant kernel of the FP64 sweeps)
+    names = pc.KERNEL_NAMES
+    kname = max(names, key=lambda k: ktimes[k][1])
     launches_c, ms_c = ktimes["contract"]
-    sweeps = int(iters.sum()) * args.steps                 # trajectory-sweeps over the timed steps
-    flops = contract_flops_per_sweep(w.N) * sweeps
+    sweeps64 = ktimes["sweeps64"]
+    flops = contract_flops_per_sweep(w.N) * sweeps64
     achieved = flops / (ms_c / 1000.0) / 1e12 if ms_c > 0 else 0.0
     peak, peak_src = fp64_tensor_peak_tflops()
+    tsum = sum(ktimes[k][1] for k in names)
+    traffic = None if TRAFFIC_BYTES_PER_SWEEP is None else TRAFFIC_BYTES_PER_SWEEP * sweeps64 / max(1, launches_c)
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-            "kernel": "k_contract (FP64 DMMA m16n8k4)", "dtype": "f64", "peak_source": peak_src,
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "kernel": "k_contract (FP64 DMMA mma.sync m16n8k4)", "dtype": "f64", "peak_source": peak_src,
             "launches": launches_c, "avg_launch_us": 1000.0 * ms_c / max(1, launches_c),
             "algorithmic_flops_per_launch": flops / max(1, launches_c),
-            "kernel_share": {k: v[1] / max(1e-9, sum(x[1] for x in ktimes.values())) for k, v in ktimes.items()},
+            "kernel_share": {k: ktimes[k][1] / max(1e-9, tsum) for k in names},
             "dominant_by_time": kname}
 
     line = None
@@ -306,23 +342,37 @@ def run_ours(args, world, rank, local):
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"first {min(M, args.cpu_sample)} trajectories of the workload, full 4-year arcs, "
                              f"{secs:.1f} s on {cores} threads"}
+        stats = {"sweep_rounds_per_step": rounds_total / max(1, args.steps),
+                 "trajectory_sweeps_fp64_per_step": sweeps64 / max(1, args.steps),
+                 "trajectory_sweeps_fp32_per_step": ktimes["sweeps32"] / max(1, args.steps),
+                 "status_nonzero": int((status != 0).sum()),
+                 "kernel_ms_per_step": {k: ktimes[k][1] / args.steps for k in names}}
+        if plain is not None:
+            stats["plain_fp64"] = {
+                "value": total_ic / (plain["ms"] / 1000.0), "unit": UNIT, "ms_per_step": plain["ms"],
+                "steps": args.plain_steps, "sweep_rounds_per_step": plain["rounds"],
+                "trajectory_sweeps_fp64_per_step": plain["kt"]["sweeps64"] / max(1, args.plain_steps),
+                "kernel_ms_per_step": {k: plain["kt"][k][1] / args.plain_steps for k in names},
+                "speedup_mixed_over_plain": plain["ms"] / ms}
+            stats["mixed_vs_plain_fp64_rel_err"] = {
+                "pos_max": float(plain["er"].max()), "pos_median": float(np.median(plain["er"])),
+                "vel_max": float(plain["ev"].max()), "vel_median": float(np.median(plain["ev"]))}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_ic_per_gpu": M, "N": w.N, "arc_years": 4, "tol": w.tol,
-                       "path": "plain FP64 batched sweep (per-trajectory segments, DMMA contraction)",
+                       "path": ("mixed FP32->FP64 batched sweep" if mixed else "plain FP64 batched sweep")
+                               + " (per-trajectory segments, compaction, DMMA contraction)",
+                       "switch_tol": args.switch_tol if mixed else None,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx0.numel() * 8),
                     "d2h_bytes_per_step": int(hxf.numel() * 8 + hst.numel() * 4)},
-            "gpu_launches": int(sum(v[0] for v in ktimes.values()) + 2 * args.steps),
+            "gpu_launches": int(ktimes["kernel_launches"]),
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
-            "stats": {"sweep_rounds_per_step": rounds_total / max(1, args.steps),
-                      "trajectory_sweeps_per_step": int(iters.sum()),
-                      "status_nonzero": int((status != 0).sum()),
-                      "kernel_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()}},
+            "stats": stats,
         }
         print(json.dumps(line))
     plan.close()
@@ -340,6 +390,11 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--ref-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--switch-tol", type=float, default=0.0,
+                    help="FP32 -> FP64 switch threshold (0: when the FP32 change stops falling)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--plain-steps", type=int, default=3)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":

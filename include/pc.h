@@ -83,8 +83,9 @@ typedef struct {
 } pc_ephemeris;
 
 #define PC_PREC_FP64 0   /* every sweep in FP64 */
-#define PC_PREC_MIXED 1  /* FP32 sweeps on the deviation from the warm start until the change is below
-                            switch_tol, then FP64 sweeps to tol (not in the paper: an extension) */
+#define PC_PREC_MIXED 1  /* each segment first runs FP32 sweeps on the deviation from its warm start
+                            until the change is below switch_tol or stops falling, then FP64 sweeps
+                            to tol (not in the paper: an extension); needs N <= 287 */
 
 typedef struct {
   double tol;          /* stopping tolerance on the sweep-to-sweep change (overridden per call) */
@@ -99,13 +100,14 @@ typedef struct {
   double div_limit;    /* a change above this, or non-finite, fails the attempt */
   double trunc_tol;    /* resolution test on the Chebyshev tail of the force fit (<= 0 disables) */
   int precision;       /* PC_PREC_FP64 or PC_PREC_MIXED */
-  double switch_tol;   /* mixed precision: FP32 sweeps until the change is below this */
+  double switch_tol;   /* mixed precision: FP32 sweeps until the change is below this (0: until the
+                          FP32 change stops falling) */
   long long max_rounds;/* safety cap on sweep rounds per call (0 = 10,000,000) */
 } pc_options;
 
 /* Fills *o with the defaults: tol 1e-13, relative 1, max_iters 60, max_depth 8,
  * warm_start 1, seg_mode 0, truncated 0, stall_sweeps 5, stall_factor 1e3,
- * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 1e-6, max_rounds 0.
+ * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0.
  * Returns PC_EINVAL if o is NULL. */
 pc_status pc_options_default(pc_options *o);
 
@@ -202,20 +204,25 @@ pc_status pc_apply_operator_static(pc_plan *plan, long long n_ic, const double *
  * elapsed times are summed when pc_plan_kernel_times is called (not during the
  * propagation, so the host adds no gap to the timed work). */
 #define PC_KERNEL_SETUP 0     /* new segments: node times, ephemeris, warm start */
-#define PC_KERNEL_FORCE 1     /* F = omega2 f(Y, t) */
-#define PC_KERNEL_CONTRACT 2  /* Y' = x0 + K F and the per-trajectory change */
-#define PC_KERNEL_CONTROL 3   /* stop tests, segment accept / halve / advance */
-#define PC_KERNEL_KINDS 4
+#define PC_KERNEL_FP32 1      /* mixed precision: the FP32 sweeps of new segments */
+#define PC_KERNEL_FORCE 2     /* FP64 sweeps: F = omega2 f(Y, t) */
+#define PC_KERNEL_CONTRACT 3  /* FP64 sweeps: Y' = x0 + K F and the per-trajectory change */
+#define PC_KERNEL_CONTROL 4   /* stop tests, segment accept / halve / advance */
+#define PC_KERNEL_KINDS 5
 typedef struct {
   long long launches[PC_KERNEL_KINDS];
   double ms[PC_KERNEL_KINDS]; /* summed device time */
+  long long sweeps64;         /* trajectory-sweeps done in FP64 */
+  long long sweeps32;         /* trajectory-sweeps done in FP32 (mixed precision) */
+  long long kernel_launches;  /* device kernels the library launched */
 } pc_kernel_times;
 
 /* on != 0 turns per-kernel event recording on for later calls. */
 pc_status pc_plan_set_profiling(pc_plan *plan, int on);
 
 /* Sums the recorded intervals into *out (after synchronizing the recorded
- * events) and clears them. */
+ * events) and clears them.  The sweep and launch counts cover every call since
+ * the previous pc_plan_kernel_times, whether profiling was on or not. */
 pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
 
 /* Copies the plan's operator K ((N+1) x (N+1), row-major) and nodes tau (N+1)

@@ -33,10 +33,11 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
     const double lo = md.t_begin, hi = md.t_begin + md.granule * md.n_gr;
     if (std::fmin(t0, tf) < lo || std::fmax(t0, tf) > hi) return PC_EINVAL;
   }
-  pc_status ps = ensure_workspace(p, n_ic);
+  const pc_options &o = p->opt;
+  const int mixed = o.precision == PC_PREC_MIXED ? 1 : 0;
+  pc_status ps = ensure_workspace(p, n_ic, mixed);
   if (ps != PC_OK) return ps;
   cudaStream_t st = (cudaStream_t)stream;
-  const pc_options &o = p->opt;
   Sweep s{};
   s.N = p->N;
   s.n = p->n;
@@ -66,9 +67,16 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
   s.status = status;
   s.iters = iters;
   s.nseg = nseg;
+  s.mixed = mixed;
+  s.switch_tol = o.switch_tol;
   s.list[0] = w.lists;
   s.list[1] = w.lists + w.ld;
   s.list_cnt = w.ints + 2;
+  s.l64[0] = w.lists + 2 * (size_t)w.ld;
+  s.l64[1] = w.lists + 3 * (size_t)w.ld;
+  s.l64_cnt = w.ints + 5;
+  s.tile_ctr = w.ints + 7;
+  s.cnt64 = w.cnt64;
   s.list_cur = 0;
   s.A = (int)n_ic;
   w.live = 0;
@@ -84,14 +92,14 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
     for (int r = 0; r < kRoundsPerBatch && e == cudaSuccess && s.A > 0; r++) {
       cudaEvent_t *ev = nullptr;
       if (p->prof_on) {
-        const size_t need = (size_t)(p->prof_rounds + 1) * 5;
+        const size_t need = (size_t)(p->prof_rounds + 1) * 6;
         while (e == cudaSuccess && p->prof_ev.size() < need) {
           cudaEvent_t x;
           e = cudaEventCreate(&x);
           if (e == cudaSuccess) p->prof_ev.push_back(x);
         }
         if (e != cudaSuccess) break;
-        ev = p->prof_ev.data() + (size_t)p->prof_rounds * 5;
+        ev = p->prof_ev.data() + (size_t)p->prof_rounds * 6;
         p->prof_rounds++;
       }
       e = launch_round(p, s, cur, st, ev);
@@ -135,9 +143,13 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
   if (e == cudaSuccess && capped) e = launch_abort(p, s, st);
   // aggregate: did any trajectory stop early?
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints, w.ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.h_cnt64, w.cnt64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (rounds_out) *rounds_out = rounds;
   if (e != cudaSuccess) return cuda_status(e);
+  p->acc_sweeps64 += (long long)w.h_cnt64[0];
+  p->acc_sweeps32 += (long long)w.h_cnt64[1];
   if (capped || w.h_ints[1] > 0) return PC_ENOTCONV;
   return PC_OK;
 }
@@ -174,7 +186,7 @@ extern "C" pc_status pc_apply_operator(pc_plan *p, long long n_ic, const double 
                                        void *stream) {
   if (!p || n_ic < 0 || (n_ic > 0 && (!x0 || !g || !y))) return PC_EINVAL;
   if (n_ic == 0) return PC_OK;
-  pc_status ps = ensure_workspace(p, n_ic);
+  pc_status ps = ensure_workspace(p, n_ic, 0);
   if (ps != PC_OK) return ps;
   cudaStream_t st = (cudaStream_t)stream;
   Workspace &w = p->ws;
@@ -203,8 +215,8 @@ extern "C" pc_status pc_plan_kernel_times(pc_plan *p, pc_kernel_times *out) {
   }
   cudaError_t e = cudaSuccess;
   for (long long r = 0; r < p->prof_rounds && e == cudaSuccess; r++) {
-    cudaEvent_t *ev = p->prof_ev.data() + (size_t)r * 5;
-    e = cudaEventSynchronize(ev[4]);
+    cudaEvent_t *ev = p->prof_ev.data() + (size_t)r * 6;
+    e = cudaEventSynchronize(ev[5]);
     for (int k = 0; k < PC_KERNEL_KINDS && e == cudaSuccess; k++) {
       float ms = 0.f;
       e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
@@ -213,5 +225,10 @@ extern "C" pc_status pc_plan_kernel_times(pc_plan *p, pc_kernel_times *out) {
     }
   }
   p->prof_rounds = 0;
+  out->sweeps64 = p->acc_sweeps64;
+  out->sweeps32 = p->acc_sweeps32;
+  out->kernel_launches = p->acc_launches;
+  p->acc_sweeps64 = p->acc_sweeps32 = 0;
+  p->acc_launches = 0;
   return cuda_status(e);
 }

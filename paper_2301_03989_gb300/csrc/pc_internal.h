@@ -11,9 +11,15 @@ namespace pcx {
 
 constexpr int kMaxBodies = 32;
 constexpr int kMaxN = 512;
+constexpr int kMaxNpl = 9;   // mixed precision: N + 1 <= 32 * kMaxNpl (N <= 287)
 
-// Trajectory phases.
-enum : int { PH_ITER = 0, PH_DONE = 1 };
+// Floats per node in the FP32 record of a new segment (mixed precision):
+// float4 groups (r_K, mu_c/|r_K|^3), (v_K, -), (indirect term, -), then one
+// (r_K - r_b, -) per body.  Shared by the allocation and the kernels.
+__host__ __device__ constexpr int x32_stride(int B) { return 12 + 4 * B; }
+
+// Trajectory phases: FP64 sweeps, finished, FP32 sweeps (mixed precision).
+enum : int { PH_ITER = 0, PH_DONE = 1, PH_ITER32 = 2 };
 
 // Segment-attempt outcomes.
 enum : int { SEG_CONTINUE = -1, SEG_OK = 0, SEG_STALLED = 1, SEG_FAIL_CAP = 2, SEG_FAIL_DIV = 3, SEG_FAIL_TRUNC = 4 };
@@ -37,12 +43,13 @@ struct Ctl {
   double *hbase;      // base segment length
   double *ta, *tb, *w1, *w2;
   double *e_best;
-  unsigned long long *err;  // this round's max change, as non-negative double bits
+  unsigned long long *err;  // this round's max change (FP64 phase), non-negative double bits
   long long *p;       // segment start, in units of hbase / 2^max_depth
   int *depth, *phase, *status, *sweeps, *seg_sweeps, *nstall, *nseg, *need_setup, *last, *ic;
+  unsigned *err32;    // final FP32-phase change of a trajectory whose FP32 phase blew up
 };
-constexpr int kCtlDoubles = 13;  // x[6] + hbase, ta, tb, w1, w2, e_best, spare
-constexpr int kCtlInts = 10;
+constexpr int kCtlDoubles = 12;  // x[6] + hbase, ta, tb, w1, w2, e_best
+constexpr int kCtlInts = 11;     // 10 ints + err32
 
 // Sweep parameters of one call.
 struct Sweep {
@@ -53,33 +60,46 @@ struct Sweep {
   double t0, tf, total, sgn;
   int segments, seg_mode, max_depth, max_iters, stall_sweeps, relative, warm;
   double tol, stall_factor, div_limit, trunc_tol;
+  int mixed;                 // 1: segments start with FP32 sweeps
+  double switch_tol;         // FP32 -> FP64 when the FP32 change is below this
   int max_ckpt;
   double *ckpt;              // [n_ic][max_ckpt][7] or nullptr
   // outputs, indexed by trajectory, written when a trajectory finishes
   double *xf;                // [6][n_ic]
   int *status, *iters, *nseg;
-  // new-segment lists: setup of round r reads list (r & 1) and the control of
-  // round r appends to list ((r + 1) & 1)
-  int *list[2];
+  // Per-round lists, double-buffered by round parity: round r reads list
+  // [r & 1] and its control kernel fills list [(r + 1) & 1].
+  int *list[2];              // trajectories starting a new segment (setup)
   int *list_cnt;             // [2]
+  int *l64[2];               // trajectories doing an FP64 sweep
+  int *l64_cnt;              // [2]
   int list_cur;
+  int *tile_ctr;             // dynamic tile counter of the FP64 contraction
+  unsigned long long *cnt64; // [0] FP64, [1] FP32 trajectory-sweeps of this call
 };
 
 struct Workspace {
   long long cap = 0;         // slots the buffers hold
   int ld = 0;
-  double *Y[2] = {nullptr, nullptr};  // [n][6][ld]; the other buffer receives a repack
+  double *Y[2] = {nullptr, nullptr};  // [n][6][ld] FP64 iterate (current / next; also repack target)
   double *G = nullptr;       // [kpad][6][ld]; rows n..kpad-1 stay zero
   double *E[2] = {nullptr, nullptr};    // [n][B][3][ld] body positions at the nodes (+ repack target)
   double *Aind[2] = {nullptr, nullptr}; // [n][3][ld] summed indirect acceleration (+ repack target)
+  // mixed precision (allocated when the plan asks for it), by new-segment list entry
+  double *YK = nullptr;      // [entry][n][6] FP64 warm start
+  float *X32 = nullptr;      // [entry][n][x32_stride(B)] FP32 node records
   Ctl ctl[2]{};              // live control state and repack target
   void *ctl_block[2] = {nullptr, nullptr};
-  int *lists = nullptr;      // 2 x ld slot lists
-  int *ints = nullptr;       // [0..1] done counters [finished, stopped], [2..3] list counts, [4] repack count
+  int *lists = nullptr;      // 4 x ld: setup lists [2], FP64 lists [2]
+  int *ints = nullptr;       // [0..1] done counters [finished, stopped], [2..3] setup list counts,
+                             // [4] repack count, [5..6] FP64 list counts, [7] tile counter
   int *pos = nullptr;        // [ld] repack destinations
+  unsigned long long *cnt64 = nullptr;  // [0] FP64 trajectory-sweeps, [1] FP32 trajectory-sweeps
+  unsigned long long *h_cnt64 = nullptr;
   int *h_ints = nullptr;     // pinned host mirror: 2 slots of 8 ints, [16] repack count
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  int live = 0;              // which of E/Aind/ctl is live
+  int live = 0;              // which of E/Aind/ctl/YK/... is live
+  int mixed = 0;             // mixed-precision buffers present
 };
 
 }  // namespace pcx
@@ -92,22 +112,27 @@ struct pc_plan {
   // model (device copies)
   pcx::Model model{};
   double *d_mu = nullptr, *d_coef = nullptr;
+  float *d_mu32 = nullptr;   // GMs rounded to FP32 (mixed precision)
   // operator: rows are nodes 1..N (row r <-> node r+1), padded to rows_pad x kpad, zeros outside
   double *d_K = nullptr;
+  float *d_K32T = nullptr;   // the operator rounded to FP32 and transposed, [N+1][32 npl]
+  int npl = 0;               // nodes per lane of the FP32 warp kernel, ceil((N+1)/32) (0: no mixed path)
   double *d_tau = nullptr;   // [n]
   double *h_K = nullptr;     // host copy, (N+1) x (N+1)
   double *h_tau = nullptr;   // [n]
   pcx::Workspace ws;
-  // per-kernel timing: 5 events per recorded round (before setup, force,
-  // contract, control, after control)
+  // per-kernel timing: 6 events per recorded round (before setup, force,
+  // contract, the FP32 kernels, control, after control)
   int prof_on = 0;
   std::vector<cudaEvent_t> prof_ev;
   long long prof_rounds = 0;
+  long long acc_sweeps64 = 0, acc_sweeps32 = 0;  // since the last pc_plan_kernel_times
+  mutable long long acc_launches = 0;
 };
 
 namespace pcx {
 // pc_plan.cu
-pc_status ensure_workspace(pc_plan *plan, long long n_ic);
+pc_status ensure_workspace(pc_plan *plan, long long n_ic, int mixed);
 void free_workspace(pc_plan *plan);
 // pc_sweep.cu
 cudaError_t launch_init(const pc_plan *plan, const Sweep &s, const double *x0, cudaStream_t st);

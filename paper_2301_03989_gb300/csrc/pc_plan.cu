@@ -82,7 +82,7 @@ extern "C" pc_status pc_options_default(pc_options *o) {
   o->div_limit = 1e3;
   o->trunc_tol = 1e-13;
   o->precision = PC_PREC_FP64;
-  o->switch_tol = 1e-6;
+  o->switch_tol = 0.0;
   o->max_rounds = 0;
   return PC_OK;
 }
@@ -90,7 +90,8 @@ extern "C" pc_status pc_options_default(pc_options *o) {
 static pc_status check_options(const pc_options &o) {
   if (!(o.tol >= 0.0) || o.max_iters < 1 || o.max_depth < 0 || o.max_depth > 30 || o.stall_sweeps < 1 ||
       !(o.stall_factor >= 0.0) || !(o.div_limit > 0.0) || (o.seg_mode != 0 && o.seg_mode != 1) ||
-      (o.precision != PC_PREC_FP64 && o.precision != PC_PREC_MIXED) || o.max_rounds < 0)
+      (o.precision != PC_PREC_FP64 && o.precision != PC_PREC_MIXED) || o.max_rounds < 0 ||
+      !(o.switch_tol >= 0.0))
     return PC_EINVAL;
   return PC_OK;
 }
@@ -111,6 +112,7 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
   pc_options_default(&o);
   if (opt) o = *opt;
   if (check_options(o) != PC_OK) return PC_EINVAL;
+  if (o.precision == PC_PREC_MIXED && N + 1 > 32 * kMaxNpl) return PC_EINVAL;
 
   pc_plan *p = new (std::nothrow) pc_plan();
   if (!p) return PC_ENOMEM;
@@ -137,6 +139,17 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
     for (int k = 0; k < n; k++) Kd[(size_t)r * p->kpad + k] = p->h_K[(size_t)(r + 1) * n + k];
   cudaError_t e = dalloc(&p->d_K, Kd.size());
   if (e == cudaSuccess) e = cudaMemcpy(p->d_K, Kd.data(), sizeof(double) * Kd.size(), cudaMemcpyHostToDevice);
+  // FP32 operator for the mixed-precision warp kernel: K32T[k][j] = K[j][k]
+  // for output nodes j = 0..N laid out as 32 lanes x npl, zero elsewhere.
+  if (N + 1 <= 32 * kMaxNpl) {
+    p->npl = (N + 32) / 32;
+    const int np = 32 * p->npl;
+    std::vector<float> Kt((size_t)n * np, 0.0f);
+    for (int k = 0; k < n; k++)
+      for (int j = 0; j <= N; j++) Kt[(size_t)k * np + j] = (float)p->h_K[(size_t)j * n + k];
+    if (e == cudaSuccess) e = dalloc(&p->d_K32T, Kt.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_K32T, Kt.data(), sizeof(float) * Kt.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = dalloc(&p->d_tau, n);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_tau, p->h_tau, sizeof(double) * n, cudaMemcpyHostToDevice);
   Model &m = p->model;
@@ -151,6 +164,10 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
     size_t nc = (size_t)B * ephem->n_granules * 3 * (ephem->degree + 1);
     if (e == cudaSuccess) e = dalloc(&p->d_mu, B);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_mu, force->mu, sizeof(double) * B, cudaMemcpyHostToDevice);
+    std::vector<float> mu32(B);
+    for (int b = 0; b < B; b++) mu32[b] = (float)force->mu[b];
+    if (e == cudaSuccess) e = dalloc(&p->d_mu32, B);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_mu32, mu32.data(), sizeof(float) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = dalloc(&p->d_coef, nc);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_coef, ephem->coef, sizeof(double) * nc, cudaMemcpyHostToDevice);
   } else {
@@ -171,7 +188,7 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
 
 namespace {
 // Carves one control block (kCtlDoubles doubles, one u64, one i64 and kCtlInts
-// ints per slot) into the Ctl arrays.
+// 4-byte fields per slot) into the Ctl arrays.
 void carve_ctl(void *block, long long ld, Ctl &t) {
   char *c = (char *)block;
   auto take = [&](size_t each) { char *r = c; c += each * ld; return r; };
@@ -182,7 +199,6 @@ void carve_ctl(void *block, long long ld, Ctl &t) {
   t.w1 = (double *)take(8);
   t.w2 = (double *)take(8);
   t.e_best = (double *)take(8);
-  take(8);  // spare double column
   t.err = (unsigned long long *)take(8);
   t.p = (long long *)take(8);
   t.depth = (int *)take(4);
@@ -195,12 +211,13 @@ void carve_ctl(void *block, long long ld, Ctl &t) {
   t.need_setup = (int *)take(4);
   t.last = (int *)take(4);
   t.ic = (int *)take(4);
+  t.err32 = (unsigned *)take(4);
 }
 }  // namespace
 
-pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
+pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic, int mixed) {
   Workspace &w = p->ws;
-  if (n_ic <= w.cap && w.Y[0]) return PC_OK;
+  if (n_ic <= w.cap && w.Y[0] && (!mixed || w.mixed)) return PC_OK;
   free_workspace(p);
   const long long ld = (n_ic + 7) / 8 * 8;
   if (ld > (1LL << 30)) return PC_EINVAL;
@@ -217,10 +234,16 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
     if (e == cudaSuccess) e = cudaMalloc(&w.ctl_block[b], ctl_bytes);
     if (e == cudaSuccess) e = cudaMemset(w.ctl_block[b], 0, ctl_bytes);
   }
-  if (e == cudaSuccess) e = dalloc(&w.lists, 2 * ld);
+  if (mixed && e == cudaSuccess) {
+    e = dalloc(&w.YK, n * 6 * ld);
+    if (e == cudaSuccess) e = dalloc(&w.X32, n * (size_t)x32_stride((int)B) * ld);
+  }
+  if (e == cudaSuccess) e = dalloc(&w.lists, 4 * ld);
   if (e == cudaSuccess) e = dalloc(&w.pos, ld);
-  if (e == cudaSuccess) e = dalloc(&w.ints, 8);
-  if (e == cudaSuccess) e = cudaMemset(w.ints, 0, sizeof(int) * 8);
+  if (e == cudaSuccess) e = dalloc(&w.cnt64, 2);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&w.h_cnt64, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess) e = dalloc(&w.ints, 16);
+  if (e == cudaSuccess) e = cudaMemset(w.ints, 0, sizeof(int) * 16);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&w.h_ints, sizeof(int) * 24);
   for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -231,6 +254,7 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic) {
   w.cap = ld;
   w.ld = (int)ld;
   w.live = 0;
+  w.mixed = mixed;
   return PC_OK;
 }
 
@@ -242,11 +266,15 @@ void pcx::free_workspace(pc_plan *p) {
     cudaFree(w.Aind[b]);
     cudaFree(w.ctl_block[b]);
   }
+  cudaFree(w.YK);
+  cudaFree(w.X32);
   cudaFree(w.G);
   cudaFree(w.lists);
   cudaFree(w.pos);
   cudaFree(w.ints);
+  cudaFree(w.cnt64);
   if (w.h_ints) cudaFreeHost(w.h_ints);
+  if (w.h_cnt64) cudaFreeHost(w.h_cnt64);
   for (int i = 0; i < 2; i++)
     if (w.ev[i]) cudaEventDestroy(w.ev[i]);
   w = Workspace();
@@ -257,8 +285,10 @@ extern "C" void pc_plan_destroy(pc_plan *p) {
   free_workspace(p);
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   cudaFree(p->d_K);
+  cudaFree(p->d_K32T);
   cudaFree(p->d_tau);
   cudaFree(p->d_mu);
+  cudaFree(p->d_mu32);
   cudaFree(p->d_coef);
   std::free(p->h_K);
   std::free(p->h_tau);

@@ -1,21 +1,26 @@
-// Device kernels of the FP64 batched Picard-Chebyshev sweep and their launchers.
+// Device kernels of the batched Picard-Chebyshev sweep and their launchers.
 //
 // One "round" advances every unfinished trajectory by one Picard sweep of its
 // own current segment (Section "Matrix form for vectorized and parallel
 // computation"; Eq. 2):
-//   k_setup    new segments only: node times, ephemeris at the nodes, Keplerian
-//              warm start (Sections "Integration concept", "Dynamics model")
-//   k_force    F = omega2 f(Y, t) at every node (the paper's dynamics kernel)
-//   k_contract Y' = 1 x0^T + K F, the (N+1)x(N+1) by (N+1)x(6M) contraction on
-//              the FP64 tensor cores (DMMA), fused with the per-trajectory
-//              change max_j max(|dr|/|r|, |dv|/|v|) (the paper's errCompute +
-//              maxReduce, Section "CPU-GPU cooperated iteration error
-//              computation", without the host round trip)
-//   k_control  per trajectory: stop test, stall and resolution tests, segment
-//              accept / halve / advance (piecewise integration, Section "Matrix
-//              form")
-// State layout: node-major, component-planar Y[j][c][m] (Section "Dynamics
-// model, array sorting, and CUDA kernel"), leading dimension ld over m.
+//   k_setup      new segments only: node times, ephemeris at the nodes,
+//                Keplerian warm start (Sections "Integration concept",
+//                "Dynamics model"), and for mixed precision the FP32 inputs
+//   k_force      FP64 phase: F = omega2 f(Y, t) (the paper's dynamics kernel)
+//   k_contract   FP64 phase: Y' = 1 x0^T + K F on the FP64 tensor cores
+//                (DMMA), fused with the per-trajectory change
+//                max_j max(|dr|/|r|, |dv|/|v|) (the paper's errCompute +
+//                maxReduce, Section "CPU-GPU cooperated iteration error
+//                computation", without the host round trip)
+//   k_fp32       mixed precision, new segments: the whole FP32 phase (force
+//                deviation from the warm start in Encke form, its contraction,
+//                the change) for one trajectory per warp, then Y = y_K + delta
+//   k_control    per trajectory: stop / switch / stall / resolution tests,
+//                segment accept / halve / advance (piecewise integration)
+// State layout: node-major, component-planar Y[j][c][slot] (Section "Dynamics
+// model, array sorting, and CUDA kernel"), leading dimension ld over slots.
+// Active trajectories occupy slots [0, A); finished ones are packed out.
+#include <algorithm>
 #include <cstdint>
 
 #include "pc_internal.h"
@@ -29,11 +34,29 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 
 // NaN-propagating maximum of non-negative values.
 __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+__device__ __forceinline__ float nanmaxf(float a, float b) { return (b > a || b != b) ? b : a; }
 
+// Non-negative doubles / floats order like their bit patterns; NaN maps to the largest.
 __device__ __forceinline__ unsigned long long err_bits(double e) {
-  // non-negative doubles order like their bit patterns; NaN maps to the largest
   if (e != e) return 0x7FF8000000000000ULL;
   return (unsigned long long)__double_as_longlong(e);
+}
+__device__ __forceinline__ unsigned err_bits32(float e) {
+  if (e != e) return 0x7FC00000u;
+  return __float_as_uint(e);
+}
+
+// Warp-aggregated append of `flag` lanes to list[] with counter *cnt.  Every
+// lane of the warp must call it.
+__device__ __forceinline__ void warp_append(bool flag, int value, int *list, int *cnt) {
+  const unsigned mask = __ballot_sync(0xffffffffu, flag);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(cnt, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (flag) list[base + __popc(mask & ((1u << lane) - 1u))] = value;
 }
 
 // ---------------------------------------------------------------------------
@@ -66,6 +89,7 @@ __device__ void schedule(const Sweep &s, Ctl &c, int m, int list_next) {
   c.seg_sweeps[m] = 0;
   c.nstall[m] = 0;
   c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);  // +inf
+  c.phase[m] = s.mixed ? PH_ITER32 : PH_ITER;
   const int k = atomicAdd(s.list_cnt + list_next, 1);
   s.list[list_next][k] = m;
 }
@@ -80,45 +104,50 @@ __device__ __forceinline__ void write_outputs(const Sweep &s, const Ctl &c, int 
 }
 
 __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, int *done) {
-  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= s.n_ic) return;
-  const int ld = s.ld;
-  double x[6];
-  bool finite = true;
-  for (int q = 0; q < 6; q++) {
-    x[q] = x0[q * s.n_ic + m];
-    c.x[q * ld + m] = x[q];
-    finite = finite && isfinite(x[q]);
-  }
-  double h = s.total / (double)s.segments;
-  if (s.seg_mode == 1 && finite) {
-    const double r0 = sqrt(dadd(dadd(dmul(x[0], x[0]), dmul(x[1], x[1])), dmul(x[2], x[2])));
-    const double v2 = dadd(dadd(dmul(x[3], x[3]), dmul(x[4], x[4])), dmul(x[5], x[5]));
-    const double alpha = dsub(2.0 / r0, v2 / md.mu_c);
-    if (alpha > 0.0) {
-      const double a = 1.0 / alpha;
-      const double twopi = 6.283185307179586;  // 2 * M_PI rounded
-      h = dmul(twopi, sqrt(dmul(dmul(a, a), a) / md.mu_c)) / (double)s.segments;
+  const long long mm = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = (int)mm;
+  bool to64 = false;
+  if (mm < s.n_ic) {
+    const int ld = s.ld;
+    double x[6];
+    bool finite = true;
+    for (int q = 0; q < 6; q++) {
+      x[q] = x0[q * s.n_ic + m];
+      c.x[q * ld + m] = x[q];
+      finite = finite && isfinite(x[q]);
+    }
+    double h = s.total / (double)s.segments;
+    if (s.seg_mode == 1 && finite) {
+      const double r0 = sqrt(dadd(dadd(dmul(x[0], x[0]), dmul(x[1], x[1])), dmul(x[2], x[2])));
+      const double v2 = dadd(dadd(dmul(x[3], x[3]), dmul(x[4], x[4])), dmul(x[5], x[5]));
+      const double alpha = dsub(2.0 / r0, v2 / md.mu_c);
+      if (alpha > 0.0) {
+        const double a = 1.0 / alpha;
+        const double twopi = 6.283185307179586;  // 2 * M_PI rounded
+        h = dmul(twopi, sqrt(dmul(dmul(a, a), a) / md.mu_c)) / (double)s.segments;
+      }
+    }
+    c.ic[m] = m;
+    c.hbase[m] = h;
+    c.p[m] = 0;
+    c.depth[m] = 0;
+    c.status[m] = finite ? 0 : PC_IC_NONFINITE;
+    c.sweeps[m] = 0;
+    c.nseg[m] = 0;
+    c.err[m] = 0ULL;
+    c.err32[m] = 0u;
+    c.need_setup[m] = 0;
+    if (!finite || !(s.total > 0.0)) {
+      c.phase[m] = PH_DONE;
+      write_outputs(s, c, m);
+      atomicAdd(done, 1);
+      if (!finite) atomicAdd(done + 1, 1);
+    } else {
+      schedule(s, c, m, s.list_cur);
+      to64 = c.phase[m] == PH_ITER;
     }
   }
-  c.ic[m] = (int)m;
-  c.hbase[m] = h;
-  c.p[m] = 0;
-  c.depth[m] = 0;
-  c.status[m] = finite ? 0 : PC_IC_NONFINITE;
-  c.sweeps[m] = 0;
-  c.nseg[m] = 0;
-  c.err[m] = 0ULL;
-  c.need_setup[m] = 0;
-  if (!finite || !(s.total > 0.0)) {
-    c.phase[m] = PH_DONE;
-    write_outputs(s, c, (int)m);
-    atomicAdd(done, 1);
-    if (!finite) atomicAdd(done + 1, 1);
-    return;
-  }
-  c.phase[m] = PH_ITER;
-  schedule(s, c, (int)m, s.list_cur);
+  warp_append(to64, m, s.l64[s.list_cur], s.l64_cnt + s.list_cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -128,22 +157,30 @@ __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, 
 // positions are the exactly rounded results of this recurrence: near a body
 // the force amplifies a position rounding difference by |r| / |r - r_b|.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ephem_at(const Model &md, double t, int b, double r[3]) {
+struct EphemLoc {
+  int g;
+  double sig;
+};
+
+__device__ __forceinline__ EphemLoc ephem_locate(const Model &md, double t) {
   int g = (int)floor((t - md.t_begin) / md.granule);
   g = g < 0 ? 0 : (g > md.n_gr - 1 ? md.n_gr - 1 : g);
   const double tg = dadd(md.t_begin, dmul((double)g, md.granule));
-  const double sig = dsub(dmul(2.0, dsub(t, tg)) / md.granule, 1.0);
-  const double s2 = dmul(2.0, sig);
+  return {g, dsub(dmul(2.0, dsub(t, tg)) / md.granule, 1.0)};
+}
+
+__device__ __forceinline__ void ephem_body(const Model &md, EphemLoc L, int b, double r[3]) {
+  const double s2 = dmul(2.0, L.sig);
   const int nc = md.deg + 1;
   for (int ax = 0; ax < 3; ax++) {
-    const double *cf = md.coef + (((size_t)b * md.n_gr + g) * 3 + ax) * nc;
+    const double *cf = md.coef + (((size_t)b * md.n_gr + L.g) * 3 + ax) * nc;
     double b1 = 0.0, b2 = 0.0;
     for (int k = nc - 1; k >= 1; k--) {
       const double b0 = dsub(dadd(cf[k], dmul(s2, b1)), b2);
       b2 = b1;
       b1 = b0;
     }
-    r[ax] = dsub(dadd(cf[0], dmul(sig, b1)), b2);
+    r[ax] = dsub(dadd(cf[0], dmul(L.sig, b1)), b2);
   }
 }
 
@@ -208,14 +245,31 @@ __device__ __forceinline__ void add_indirect(const Model &md, int b, const doubl
   for (int ax = 0; ax < 3; ax++) ind[ax] = fma(k, r[ax], ind[ax]);
 }
 
+// Mixed-precision inputs of the new segments, by list entry e (not slot):
+//   YK[e][j][6]        FP64 warm start y_K at node j
+//   X32[e][j][xs]      FP32 record of node j, in float4 groups:
+//                      (r_K, mu_c/|r_K|^3), (v_K, -), (summed indirect term, -),
+//                      then per body (r_K - r_b formed in FP64 then rounded, -)
+struct Mix {
+  double *YK;
+  float *X32;
+  int xs;          // floats per node record: 12 + 4B
+};
 // New segments: node times, body positions and summed indirect term at the
 // nodes, warm start -- only for the slots on this round's new-segment list
-// (grid-stride over list entries x nodes, entries fastest).  Also clears the
-// list the control kernel of this round will fill.
+// (grid-stride over list entries x nodes, entries fastest).  With mixed
+// precision the warm start goes to YK and the FP32 node records to X32 (both
+// by list entry) for k_fp32; otherwise the warm start is the first iterate.
+// Block 0 clears the lists this round's control kernel fills and the tile
+// counter.
 __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau, double *__restrict__ Y,
-                        double *__restrict__ E, double *__restrict__ Aind) {
+                        double *__restrict__ E, double *__restrict__ Aind, Mix mx) {
   const int cur = s.list_cur;
-  if (blockIdx.x == 0 && threadIdx.x == 0) s.list_cnt[cur ^ 1] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s.list_cnt[cur ^ 1] = 0;
+    s.l64_cnt[cur ^ 1] = 0;
+    *s.tile_ctr = 0;
+  }
   const long long count = s.list_cnt[cur];
   const int *__restrict__ list = s.list[cur];
   const long long total = count * s.n;
@@ -223,26 +277,52 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(i / count);
-    const int m = list[i - (long long)j * count];
+    const long long e = i - (long long)j * count;
+    const int m = list[e];
     const double t = dadd(c.w1[m], dmul(c.w2[m], tau[j]));
-    double ind[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < B; b++) {
-      double r[3];
-      ephem_at(md, t, b, r);
-      for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
-      if (md.indirect) add_indirect(md, b, r, ind);
-    }
-    for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
     double x0[6], y[6];
     for (int q = 0; q < 6; q++) x0[q] = c.x[q * ld + m];
     bool ok = false;
     if (j > 0 && s.warm) ok = kepler_dt(md.mu_c, x0, dsub(t, c.ta[m]), y);
-    for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = ok ? y[q] : x0[q];
+    if (!ok)
+      for (int q = 0; q < 6; q++) y[q] = x0[q];
+    float *rec = s.mixed ? mx.X32 + ((size_t)e * s.n + j) * mx.xs : nullptr;
+    const EphemLoc L = ephem_locate(md, t);
+    double ind[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < B; b++) {
+      double r[3];
+      ephem_body(md, L, b, r);
+      for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
+      if (md.indirect) add_indirect(md, b, r, ind);
+      if (rec) {
+        for (int ax = 0; ax < 3; ax++) rec[12 + 4 * b + ax] = (float)(y[ax] - r[ax]);
+        rec[15 + 4 * b] = 0.0f;
+      }
+    }
+    for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
+    if (rec) {
+      double *yk = mx.YK + ((size_t)e * s.n + j) * 6;
+      for (int q = 0; q < 6; q++) yk[q] = y[q];
+      const double rr = rsqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+      rec[0] = (float)y[0];
+      rec[1] = (float)y[1];
+      rec[2] = (float)y[2];
+      rec[3] = (float)(md.mu_c * rr * rr * rr);
+      rec[4] = (float)y[3];
+      rec[5] = (float)y[4];
+      rec[6] = (float)y[5];
+      rec[7] = 0.0f;
+      for (int ax = 0; ax < 3; ax++) rec[8 + ax] = (float)ind[ax];
+      rec[11] = 0.0f;
+    } else {
+      for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = y[q];
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Force: F[j][.][m] = omega2 * (v, a(r, t_j)).  One thread per (node, trajectory).
+// FP64 force: F[j][.][m] = omega2 * (v, a(r, t_j)).  One thread per (node,
+// FP64-list entry).
 // ---------------------------------------------------------------------------
 // Body b's position component ax is Eb[(b*3 + ax) * es]; the summed indirect
 // term component ax is Ai[ax * es].
@@ -274,18 +354,21 @@ __device__ __forceinline__ void accel(const Model &md, const double *__restrict_
 
 __global__ void k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y, const double *__restrict__ E,
                         const double *__restrict__ Aind, double *__restrict__ G) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
-  if (m >= s.A || c.phase[m] != PH_ITER) return;
+  if (i >= s.l64_cnt[s.list_cur]) return;
+  const int m = s.l64[s.list_cur][i];
   const int ld = s.ld;
   const double w2 = c.w2[m];
   const size_t yb = (size_t)j * 6 * ld + m;
-  const double r[3] = {Y[yb], Y[yb + ld], Y[yb + 2 * (size_t)ld]};
+  double y[6];
+#pragma unroll
+  for (int q = 0; q < 6; q++) y[q] = Y[yb + (size_t)q * ld];
   double a[3];
-  accel(md, E + (size_t)j * md.B * 3 * ld + m, Aind + (size_t)j * 3 * ld + m, (size_t)ld, r, a);
-  G[yb] = w2 * Y[yb + 3 * (size_t)ld];
-  G[yb + ld] = w2 * Y[yb + 4 * (size_t)ld];
-  G[yb + 2 * (size_t)ld] = w2 * Y[yb + 5 * (size_t)ld];
+  accel(md, E + (size_t)j * md.B * 3 * ld + m, Aind + (size_t)j * 3 * ld + m, (size_t)ld, y, a);
+  G[yb] = w2 * y[3];
+  G[yb + ld] = w2 * y[4];
+  G[yb + 2 * (size_t)ld] = w2 * y[5];
   G[yb + 3 * (size_t)ld] = w2 * a[0];
   G[yb + 4 * (size_t)ld] = w2 * a[1];
   G[yb + 5 * (size_t)ld] = w2 * a[2];
@@ -293,14 +376,16 @@ __global__ void k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y, 
 
 // ---------------------------------------------------------------------------
 // Contraction on the FP64 tensor cores: mma.sync m16n8k4 f64.
-// One warp computes output nodes j = 1 + 16*rt + (0..15) for 8 trajectories
-// m0..m0+7 and all six components (six 16x8 accumulators), streaming
-// K[rows][k] and G[k][c][m] fragments straight from L2/L1 -- FP64 throughput,
-// not bandwidth, bounds this kernel.  Fragment layouts (PTX ISA, mma.m16n8k4
-// .f64): with g = lane/4, t = lane%4:  A: a0 = A[g][t], a1 = A[g+8][t];
-// B: b0 = B[t][g];  C: c0,c1 = C[g][2t..2t+1], c2,c3 = C[g+8][2t..2t+1].
-// Epilogue: Y' = x0 + acc, and (unless DIAG) the per-trajectory maximum
-// change, reduced over the warp and merged with atomicMax.
+// A warp tile is output nodes j = 1 + 16*rt + (0..15) for 8 trajectories and
+// all six components (six 16x8 accumulators), streaming K[rows][k] and
+// F[k][c][m] fragments straight from L2/L1 -- FP64 throughput, not bandwidth,
+// bounds this kernel.  In the sweep the 8 trajectories are 8 consecutive
+// entries of the round's FP64 list, and warps take tiles from a counter until
+// none are left (no partial last wave).  Fragment layouts (PTX ISA,
+// mma.m16n8k4 .f64): with g = lane/4, t = lane%4:  A: a0 = A[g][t],
+// a1 = A[g+8][t];  B: b0 = B[t][g];  C: c0,c1 = C[g][2t..2t+1],
+// c2,c3 = C[g+8][2t..2t+1].  Epilogue: Y' = x0 + acc and (unless DIAG) the
+// per-trajectory maximum change, reduced over the warp, merged with atomicMax.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void dmma16x8x4(double (&d)[4], double a0, double a1, double b0) {
   asm volatile(
@@ -309,94 +394,339 @@ __device__ __forceinline__ void dmma16x8x4(double (&d)[4], double a0, double a1,
       : "d"(a0), "d"(a1), "d"(b0));
 }
 
+// One CTA of kSplit warps computes one tile; warp w accumulates the k-steps
+// [w*ks/kSplit, (w+1)*ks/kSplit) of it (ks = kpad/4 steps of 4), the partial
+// accumulators meet in shared memory and warp 0 adds them in warp order (a
+// fixed order, so results do not depend on scheduling) and runs the epilogue.
+// Splitting k cuts the latency of a tile by kSplit and spreads few tiles over
+// more SM sub-partitions.
+constexpr int kSplit = 4;
+
 template <bool DIAG>
-__global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *__restrict__ K,
-                                                  const double *__restrict__ G, const double *__restrict__ Yold,
-                                                  double *__restrict__ Ynew) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int n_rt = s.rows_pad / 16;
-  const int rt = warp % n_rt;
-  const int ct = warp / n_rt;
-  const int m0 = ct * 8;
-  const int ncols = DIAG ? (int)s.n_ic : s.A;
-  if (m0 >= ncols) return;
+__device__ __forceinline__ void contract_tile_split(const Sweep &s, const Ctl &c, const double *__restrict__ K,
+                                                    const double *__restrict__ G, const double *__restrict__ Yold,
+                                                    double *__restrict__ Ynew, int rt, int e0, int ncols,
+                                                    const int *__restrict__ map, double *part) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int ld = s.ld;
-  bool mine_active = false;
-  if (!DIAG) {
-    const int mm = m0 + g;
-    mine_active = (mm < ncols) && c.phase[mm] == PH_ITER;
-    if (!__any_sync(0xffffffffu, mine_active)) return;
-  }
+  // entry e0 + g feeds the B fragment (a past-the-end entry reuses entry e0's
+  // column; its results are never stored); entries e0 + 2t + {0,1} own C
+  const int eb = (e0 + g < ncols) ? e0 + g : e0;
+  const int mb = DIAG ? eb : map[eb];
   double acc[6][4];
 #pragma unroll
   for (int q = 0; q < 6; q++)
 #pragma unroll
     for (int i = 0; i < 4; i++) acc[q][i] = 0.0;
+  const int ks = s.kpad / 4;
+  const int kb = (w * ks) / kSplit, ke = ((w + 1) * ks) / kSplit;
   const double *Ka = K + (size_t)(rt * 16 + g) * s.kpad + t;
   const double *Kb = Ka + (size_t)8 * s.kpad;
-  const double *Gp = G + (size_t)t * 6 * ld + m0 + g;
+  const double *Gp = G + ((size_t)kb * 4 + t) * 6 * ld + mb;
   const size_t gstep = (size_t)4 * 6 * ld;
-  for (int k0 = 0; k0 < s.kpad; k0 += 4) {
+  for (int kk = kb; kk < ke; kk++) {
+    const int k0 = kk * 4;
     const double a0 = __ldg(Ka + k0), a1 = __ldg(Kb + k0);
 #pragma unroll
     for (int q = 0; q < 6; q++) dmma16x8x4(acc[q], a0, a1, __ldg(Gp + (size_t)q * ld));
     Gp += gstep;
   }
-  // epilogue
-  double emax[2] = {0.0, 0.0};
+  if (w > 0) {
+    double *pw = part + ((size_t)(w - 1) * 32 + lane) * 24;
 #pragma unroll
-  for (int h = 0; h < 2; h++) {          // row g (h=0) or g+8 (h=1)
-    const int j = 1 + rt * 16 + g + 8 * h;
+    for (int q = 0; q < 6; q++)
 #pragma unroll
-    for (int e = 0; e < 2; e++) {        // column 2t+e
-      const int m = m0 + 2 * t + e;
-      if (j > s.N || m >= ncols) continue;
-      if (!DIAG && c.phase[m] != PH_ITER) continue;
-      double yn[6];
-      const size_t base = (size_t)j * 6 * ld + m;
+      for (int i = 0; i < 4; i++) pw[q * 4 + i] = acc[q][i];
+  }
+  __syncthreads();
+  if (w == 0) {
+    for (int v = 1; v < kSplit; v++) {
+      const double *pv = part + ((size_t)(v - 1) * 32 + lane) * 24;
 #pragma unroll
-      for (int q = 0; q < 6; q++) {
-        yn[q] = c.x[q * ld + m] + acc[q][2 * h + e];
-        Ynew[base + (size_t)q * ld] = yn[q];
-      }
-      if (!DIAG) {
-        double d[6];
+      for (int q = 0; q < 6; q++)
 #pragma unroll
-        for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
-        double dr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        double dv = sqrt(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
-        if (s.relative) {
-          const double nr = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
-          const double nv = sqrt(yn[3] * yn[3] + yn[4] * yn[4] + yn[5] * yn[5]);
-          if (nr > 0.0) dr = dr / nr;
-          if (nv > 0.0) dv = dv / nv;
+        for (int i = 0; i < 4; i++) acc[q][i] += pv[q * 4 + i];
+    }
+    double emax[2] = {0.0, 0.0};
+    int mc[2];
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      const int ec = e0 + 2 * t + e;
+      mc[e] = (ec < ncols) ? (DIAG ? ec : map[ec]) : -1;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int j = 1 + rt * 16 + g + 8 * h;
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int m = mc[e];
+        if (j > s.N || m < 0) continue;
+        double yn[6];
+        const size_t base = (size_t)j * 6 * ld + m;
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+          yn[q] = c.x[q * ld + m] + acc[q][2 * h + e];
+          Ynew[base + (size_t)q * ld] = yn[q];
         }
-        emax[e] = nanmax(emax[e], nanmax(dr, dv));
+        if (!DIAG) {
+          double d[6];
+#pragma unroll
+          for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
+          double dr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          double dv = sqrt(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+          if (s.relative) {
+            const double nr = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+            const double nv = sqrt(yn[3] * yn[3] + yn[4] * yn[4] + yn[5] * yn[5]);
+            if (nr > 0.0) dr = dr / nr;
+            if (nv > 0.0) dv = dv / nv;
+          }
+          emax[e] = nanmax(emax[e], nanmax(dr, dv));
+        }
+      }
+    }
+    // node 0 is the segment's initial state
+    if (rt == 0 && g == 0) {
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int m = mc[e];
+        if (m >= 0)
+#pragma unroll
+          for (int q = 0; q < 6; q++) Ynew[(size_t)q * ld + m] = c.x[q * ld + m];
+      }
+    }
+    if (!DIAG) {
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        double v = emax[e];
+        v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 4));
+        v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 8));
+        v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 16));
+        if (g == 0 && mc[e] >= 0) atomicMax(c.err + mc[e], err_bits(v));
       }
     }
   }
-  // node 0 is the segment's initial state
-  if (rt == 0 && g == 0) {
-#pragma unroll
-    for (int e = 0; e < 2; e++) {
-      const int m = m0 + 2 * t + e;
-      if (m < ncols && (DIAG || c.phase[m] == PH_ITER))
-#pragma unroll
-        for (int q = 0; q < 6; q++) Ynew[(size_t)q * ld + m] = c.x[q * ld + m];
-    }
+  __syncthreads();  // the partials are reused by the next tile
+}
+
+// Sweep contraction over the round's FP64 list: persistent CTAs take tiles
+// (row tile fastest, so the CTAs of one column group run together and share F
+// in L1/L2) from a counter that the round's setup kernel cleared.
+__global__ void __launch_bounds__(32 * kSplit) k_contract(Sweep s, Ctl c, const double *__restrict__ K,
+                                                          const double *__restrict__ G,
+                                                          const double *__restrict__ Yold, double *__restrict__ Ynew) {
+  __shared__ double part[(kSplit - 1) * 32 * 24];
+  __shared__ int tile_sh;
+  const int ncols = s.l64_cnt[s.list_cur];
+  const int *map = s.l64[s.list_cur];
+  const int n_rt = s.rows_pad / 16;
+  const int n_tiles = n_rt * ((ncols + 7) / 8);
+  for (;;) {
+    if (threadIdx.x == 0) tile_sh = atomicAdd(s.tile_ctr, 1);
+    __syncthreads();
+    const int tile = tile_sh;
+    __syncthreads();
+    if (tile >= n_tiles) break;
+    contract_tile_split<false>(s, c, K, G, Yold, Ynew, tile % n_rt, (tile / n_rt) * 8, ncols, map, part);
   }
-  if (!DIAG) {
+}
+
+// Kernel-level entry point: the same tile code over columns 0..n_ic-1.
+__global__ void __launch_bounds__(32 * kSplit) k_contract_diag(Sweep s, Ctl c, const double *__restrict__ K,
+                                                               const double *__restrict__ G,
+                                                               double *__restrict__ Ynew) {
+  __shared__ double part[(kSplit - 1) * 32 * 24];
+  const int n_rt = s.rows_pad / 16;
+  const int ncols = (int)s.n_ic;
+  const int n_tiles = n_rt * ((ncols + 7) / 8);
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
+    contract_tile_split<true>(s, c, K, G, nullptr, Ynew, tile % n_rt, (tile / n_rt) * 8, ncols, nullptr, part);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 phase (mixed precision, an extension of the paper).  The iterate is
+// written y = y_K + delta with y_K the FP64 warm start of the segment.  The
+// Picard map gives delta' = rho + omega2 K (f(y_K + delta) - f_K), with f_K the
+// two-body derivative of y_K and rho = x0 + omega2 K f_K - y_K the operator's
+// residual on the Kepler arc (below the resolution tolerance on accepted
+// segments; dropped in this phase and restored by the FP64 sweeps that
+// follow).  The force deviation is formed without cancellation (Encke):
+//   (mu_c/|r_K|^3) [F(q) (r_K + dr) - dr],  q = dr.(2 r_K + dr)/|r_K|^2,
+//   F = 1 - (1+q)^(-3/2) = q s^2 (1 + s + s^2)/(1 + s),  s = (1+q)^(-1/2),
+// plus the bodies' terms with r - r_b = (r_K - r_b) + dr, where r_K - r_b was
+// formed in FP64 before rounding.  Its rounding error is relative to |delta|,
+// not to |y|.
+// ---------------------------------------------------------------------------
+// One warp per new segment (list entry e, slot m).  Lane l owns nodes
+// j = l + 32 i, i < NPL: it builds their force deviations and accumulates their
+// rows of the contraction, so the deviation stays in registers across sweeps;
+// the warp's force table F32[j][6] is shared through shared memory, and the
+// block stages the FP32 operator K32T ([N+1][32 NPL], transposed) in shared
+// memory when KSMEM.  The sweeps stop when the change is below switch_tol,
+// fails to halve the best change for two sweeps (the FP32 floor) or reaches
+// max_iters: then Y = y_K + delta is written and the trajectory joins this
+// round's FP64 list.  A non-finite or huge change leaves the trajectory in the
+// FP32 phase with that change, and the control kernel halves the segment.
+constexpr int kFp32Warps = 8;
+
+template <int NPL, bool KSMEM>
+__global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model md, const float *__restrict__ K32T,
+                                                        const float *__restrict__ mu32, double *__restrict__ Y,
+                                                        Mix mx) {
+  extern __shared__ float4 fp32_smem4[];
+  float *sm = reinterpret_cast<float *>(fp32_smem4);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int N = s.N, n = s.n, ld = s.ld, B = md.B, np = 32 * NPL;
+  const float *Kt = K32T;
+  float *Gs;
+  if (KSMEM) {
+    float *Ks = sm;
+    for (int i = threadIdx.x; i < n * np; i += blockDim.x) Ks[i] = K32T[i];
+    __syncthreads();
+    Kt = Ks;
+    Gs = sm + (size_t)n * np + (size_t)wib * n * 6;
+  } else {
+    Gs = sm + (size_t)wib * n * 6;
+  }
+  const int cur = s.list_cur;
+  const int count = s.list_cnt[cur];
+  for (int e = blockIdx.x * kFp32Warps + wib; e < count; e += gridDim.x * kFp32Warps) {
+    const int m = s.list[cur][e];
+    const float w2f = (float)c.w2[m];
+    const float *recs = mx.X32 + (size_t)e * n * mx.xs;
+    float dl[NPL][6];
 #pragma unroll
-    for (int e = 0; e < 2; e++) {
-      double v = emax[e];
-      v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 4));
-      v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 8));
-      v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, 16));
-      const int m = m0 + 2 * t + e;
-      if (g == 0 && m < ncols && c.phase[m] == PH_ITER) atomicMax(c.err + m, err_bits(v));
+    for (int i = 0; i < NPL; i++)
+#pragma unroll
+      for (int q = 0; q < 6; q++) dl[i][q] = 0.0f;
+    float ebest = __int_as_float(0x7f800000);
+    int nst = 0, it = 0;
+    bool fail = false;
+    float efin = 0.0f;
+    for (;;) {
+      // force deviation at the lane's nodes
+#pragma unroll
+      for (int i = 0; i < NPL; i++) {
+        const int j = lane + 32 * i;
+        if (j > N) break;
+        const float4 *rc = reinterpret_cast<const float4 *>(recs + (size_t)j * mx.xs);
+        const float4 rk = rc[0];
+        const float d0 = dl[i][0], d1 = dl[i][1], d2 = dl[i][2];
+        const float rr = rk.x * rk.x + rk.y * rk.y + rk.z * rk.z;
+        const float qn = (d0 * (2.0f * rk.x + d0) + d1 * (2.0f * rk.y + d1) + d2 * (2.0f * rk.z + d2)) / rr;
+        const float sq = rsqrtf(1.0f + qn);
+        const float F = qn * sq * sq * (1.0f + sq + sq * sq) / (1.0f + sq);
+        float a0 = rk.w * (F * (rk.x + d0) - d0);
+        float a1 = rk.w * (F * (rk.y + d1) - d1);
+        float a2 = rk.w * (F * (rk.z + d2) - d2);
+        for (int b = 0; b < B; b++) {
+          const float4 D = rc[3 + b];
+          const float x0 = D.x + d0, x1 = D.y + d1, x2 = D.z + d2;
+          const float ds = rsqrtf(x0 * x0 + x1 * x1 + x2 * x2);
+          const float kb = mu32[b] * ds * ds * ds;
+          a0 -= kb * x0;
+          a1 -= kb * x1;
+          a2 -= kb * x2;
+        }
+        if (md.indirect) {
+          const float4 ai = rc[2];
+          a0 -= ai.x;
+          a1 -= ai.y;
+          a2 -= ai.z;
+        }
+        float2 *g = reinterpret_cast<float2 *>(Gs + (size_t)j * 6);
+        g[0] = make_float2(w2f * dl[i][3], w2f * dl[i][4]);
+        g[1] = make_float2(w2f * dl[i][5], w2f * a0);
+        g[2] = make_float2(w2f * a1, w2f * a2);
+      }
+      __syncwarp();
+      float acc[NPL][6];
+#pragma unroll
+      for (int i = 0; i < NPL; i++)
+#pragma unroll
+        for (int q = 0; q < 6; q++) acc[i][q] = 0.0f;
+#pragma unroll 2
+      for (int k = 0; k < n; k++) {
+        const float2 *g2 = reinterpret_cast<const float2 *>(Gs + k * 6);
+        const float2 ga = g2[0], gb = g2[1], gc = g2[2];
+        const float g[6] = {ga.x, ga.y, gb.x, gb.y, gc.x, gc.y};
+        const float *kr = Kt + (size_t)k * np + lane;
+#pragma unroll
+        for (int i = 0; i < NPL; i++) {
+          const float kv = KSMEM ? kr[32 * i] : __ldg(kr + 32 * i);
+#pragma unroll
+          for (int q = 0; q < 6; q++) acc[i][q] = fmaf(kv, g[q], acc[i][q]);
+        }
+      }
+      __syncwarp();
+      float emax = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NPL; i++) {
+        const int j = lane + 32 * i;
+        if (j > N) break;
+        const float4 *rc = reinterpret_cast<const float4 *>(recs + (size_t)j * mx.xs);
+        const float4 rk = rc[0], vk = rc[1];
+        const float yk[6] = {rk.x, rk.y, rk.z, vk.x, vk.y, vk.z};
+        float d[6], y[6];
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+          d[q] = acc[i][q] - dl[i][q];
+          y[q] = yk[q] + acc[i][q];
+          dl[i][q] = acc[i][q];
+        }
+        float dr = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        float dv = sqrtf(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+        if (s.relative) {
+          const float nr = sqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+          const float nv = sqrtf(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
+          if (nr > 0.0f) dr /= nr;
+          if (nv > 0.0f) dv /= nv;
+        }
+        emax = nanmaxf(emax, nanmaxf(dr, dv));
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) emax = nanmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      it++;
+      efin = emax;
+      if (!((double)emax <= s.div_limit)) {
+        fail = true;
+        break;
+      }
+      // progress = at least halving the best change so far; at the FP32 floor
+      // the change only fluctuates, and two sweeps without progress end the phase
+      if (emax < 0.5f * ebest) {
+        nst = 0;
+      } else {
+        nst++;
+      }
+      ebest = fminf(ebest, emax);
+      if ((double)emax < s.switch_tol || nst >= 2 || it >= s.max_iters) break;
     }
+    if (!fail) {
+#pragma unroll
+      for (int i = 0; i < NPL; i++) {
+        const int j = lane + 32 * i;
+        if (j > N) break;
+        const double *yk = mx.YK + ((size_t)e * n + j) * 6;
+#pragma unroll
+        for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = yk[q] + (double)dl[i][q];
+      }
+    }
+    if (lane == 0) {
+      c.sweeps[m] += it;
+      atomicAdd(s.cnt64 + 1, (unsigned long long)it);
+      if (fail) {
+        c.err32[m] = err_bits32(efin);
+      } else {
+        c.phase[m] = PH_ITER;
+        c.seg_sweeps[m] = 0;
+        c.nstall[m] = 0;
+        c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);
+        const int k = atomicAdd(s.l64_cnt + cur, 1);
+        s.l64[cur][k] = m;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -406,12 +736,11 @@ __global__ void __launch_bounds__(256) k_contract(Sweep s, Ctl c, const double *
 // top coefficients of the interpolant of g are
 //   a_N = (1/N) sum''_j (-1)^(N+j) g_j,   a_{N-1} = (2/N) sum''_j (-1)^(N+j) tau_j g_j
 // (sum'' halves the end terms).  The integrated error is about
-// 2 |omega2| (|a_{N-1}| + |a_N|) per unit of g; G already carries omega2.
+// 2 |omega2| (|a_{N-1}| + |a_N|) per unit of g; F already carries omega2.
 // Position components are measured against max_j |r_j|, velocity ones against
-// max_j |v_j| (relative mode).
+// max_j |v_j| (relative mode).  Warp-cooperative: lanes split the nodes of slot
+// m, the sums are reduced across the warp and every lane returns the estimate.
 // ---------------------------------------------------------------------------
-// Warp-cooperative: lanes split the nodes of slot m, the sums are reduced
-// across the warp and every lane returns the estimate.
 __device__ double warp_tail_estimate(const Sweep &s, const double *__restrict__ tau, const double *__restrict__ G,
                                      const double *__restrict__ Y, int m) {
   const int ld = s.ld, N = s.N, lane = threadIdx.x & 31;
@@ -458,38 +787,50 @@ __device__ double warp_tail_estimate(const Sweep &s, const double *__restrict__ 
   return nanmax(er, ev);
 }
 
-// Per-trajectory decisions after a sweep.  Same rules, same order as the
-// oracle: blow-up, tolerance, stall, cap; then the resolution test on an
-// accepted segment; accept (advance, grow one level) or fail (halve).  A
-// finished trajectory writes its outputs.  The block size is a multiple of 32
-// and every lane reaches the warp-cooperative resolution test.
+// Per-trajectory decisions after a sweep.  FP64 phase: same rules, same order
+// as the oracle (blow-up, tolerance, stall, cap; then the resolution test on an
+// accepted segment; accept or halve).  A trajectory still in the FP32 phase
+// failed it (blow-up) and is halved.  Finished trajectories write their outputs.  Trajectories doing an FP64 sweep next
+// round go on the next FP64 list.  The block size is a multiple of 32 and every
+// lane reaches the warp-cooperative steps.
 __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const double *__restrict__ G,
                           const double *__restrict__ Ynew, int *done) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const bool act = m < s.A && c.phase[m] == PH_ITER;
+  const int phase = (m < s.A) ? c.phase[m] : PH_DONE;
+  const bool act = phase == PH_ITER || phase == PH_ITER32;
   const int ld = s.ld;
+  const int list_next = s.list_cur ^ 1;
   int out = SEG_CONTINUE;
-  int ss = 0;
+  {
+    const unsigned n64 = __popc(__ballot_sync(0xffffffffu, phase == PH_ITER));
+    if (lane == 0 && n64) atomicAdd(s.cnt64, (unsigned long long)n64);
+  }
   if (act) {
     c.need_setup[m] = 0;
-    const double e = __longlong_as_double((long long)c.err[m]);
-    c.err[m] = 0ULL;
-    ss = ++c.seg_sweeps[m];
-    c.sweeps[m] += 1;
-    if (!(e <= s.div_limit)) {
-      out = SEG_FAIL_DIV;
-    } else if (e < s.tol) {
-      out = SEG_OK;
-    } else {
-      if (e < c.e_best[m]) {
-        c.e_best[m] = e;
-        c.nstall[m] = 0;
+    if (phase == PH_ITER) {
+      c.sweeps[m] += 1;
+      const double e = __longlong_as_double((long long)c.err[m]);
+      c.err[m] = 0ULL;
+      const int ss = ++c.seg_sweeps[m];
+      if (!(e <= s.div_limit)) {
+        out = SEG_FAIL_DIV;
+      } else if (e < s.tol) {
+        out = SEG_OK;
       } else {
-        c.nstall[m] += 1;
+        if (e < c.e_best[m]) {
+          c.e_best[m] = e;
+          c.nstall[m] = 0;
+        } else {
+          c.nstall[m] += 1;
+        }
+        if (c.nstall[m] >= s.stall_sweeps && c.e_best[m] < s.stall_factor * s.tol) out = SEG_STALLED;
+        else if (ss >= s.max_iters) out = SEG_FAIL_CAP;
       }
-      if (c.nstall[m] >= s.stall_sweeps && c.e_best[m] < s.stall_factor * s.tol) out = SEG_STALLED;
-      else if (ss >= s.max_iters) out = SEG_FAIL_CAP;
+    } else {
+      // still in the FP32 phase after k_fp32: its change blew up
+      c.err32[m] = 0u;
+      out = SEG_FAIL_DIV;
     }
   }
   const bool want_tail = act && (out == SEG_OK || out == SEG_STALLED) && s.trunc_tol > 0.0;
@@ -502,54 +843,56 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const 
     const double tl = warp_tail_estimate(s, tau, G, Ynew, mb);
     if (lane == b) my_tail = tl;
   }
-  if (!act || out == SEG_CONTINUE) return;
-  if (want_tail && !(my_tail <= s.trunc_tol)) out = SEG_FAIL_TRUNC;
-  const int D = s.max_depth;
-  const int list_next = s.list_cur ^ 1;
-  bool accept = (out == SEG_OK || out == SEG_STALLED);
-  if (out == SEG_FAIL_TRUNC && c.depth[m] >= D) {
-    accept = true;
-    c.status[m] |= PC_IC_UNRESOLVED;
+  if (act && out != SEG_CONTINUE) {
+    if (want_tail && !(my_tail <= s.trunc_tol)) out = SEG_FAIL_TRUNC;
+    const int D = s.max_depth;
+    bool accept = (out == SEG_OK || out == SEG_STALLED);
+    if (out == SEG_FAIL_TRUNC && c.depth[m] >= D) {
+      accept = true;
+      c.status[m] |= PC_IC_UNRESOLVED;
+    }
+    if (accept) {
+      if (out == SEG_STALLED) c.status[m] |= PC_IC_STALLED;
+      const int k = c.nseg[m];
+      if (s.ckpt && k < s.max_ckpt) {
+        double *ck = s.ckpt + ((size_t)c.ic[m] * s.max_ckpt + k) * 7;
+        ck[0] = c.ta[m];
+        for (int q = 0; q < 6; q++) ck[1 + q] = c.x[q * ld + m];
+      }
+      const size_t last_row = (size_t)s.N * 6 * ld + m;
+      for (int q = 0; q < 6; q++) c.x[q * ld + m] = Ynew[last_row + (size_t)q * ld];
+      c.nseg[m] = k + 1;
+      c.p[m] += 1LL << (D - c.depth[m]);
+      if (c.last[m]) {
+        c.phase[m] = PH_DONE;
+        write_outputs(s, c, m);
+        atomicAdd(done, 1);
+      } else {
+        if (c.depth[m] > 0) c.depth[m] -= 1;
+        schedule(s, c, m, list_next);
+      }
+    } else {
+      c.depth[m] += 1;
+      if (c.depth[m] > D) {
+        c.status[m] |= (out == SEG_FAIL_DIV) ? PC_IC_NONFINITE : PC_IC_NOT_CONVERGED;
+        c.phase[m] = PH_DONE;
+        write_outputs(s, c, m);
+        atomicAdd(done, 1);
+        atomicAdd(done + 1, 1);
+      } else {
+        schedule(s, c, m, list_next);
+      }
+    }
   }
-  if (accept) {
-    if (out == SEG_STALLED) c.status[m] |= PC_IC_STALLED;
-    const int k = c.nseg[m];
-    if (s.ckpt && k < s.max_ckpt) {
-      double *ck = s.ckpt + ((size_t)c.ic[m] * s.max_ckpt + k) * 7;
-      ck[0] = c.ta[m];
-      for (int q = 0; q < 6; q++) ck[1 + q] = c.x[q * ld + m];
-    }
-    const size_t last_row = (size_t)s.N * 6 * ld + m;
-    for (int q = 0; q < 6; q++) c.x[q * ld + m] = Ynew[last_row + (size_t)q * ld];
-    c.nseg[m] = k + 1;
-    c.p[m] += 1LL << (D - c.depth[m]);
-    if (c.last[m]) {
-      c.phase[m] = PH_DONE;
-      write_outputs(s, c, m);
-      atomicAdd(done, 1);
-      return;
-    }
-    if (c.depth[m] > 0) c.depth[m] -= 1;
-    schedule(s, c, m, list_next);
-  } else {
-    c.depth[m] += 1;
-    if (c.depth[m] > D) {
-      c.status[m] |= (out == SEG_FAIL_DIV) ? PC_IC_NONFINITE : PC_IC_NOT_CONVERGED;
-      c.phase[m] = PH_DONE;
-      write_outputs(s, c, m);
-      atomicAdd(done, 1);
-      atomicAdd(done + 1, 1);
-      return;
-    }
-    schedule(s, c, m, list_next);
-  }
+  const bool next64 = act && c.phase[m] == PH_ITER;
+  warp_append(next64, m, s.l64[list_next], s.l64_cnt + list_next);
 }
 
 // ---- repack: move active slots to the front of the spare buffers ------------
 __global__ void k_repack_pos(int A, const int *__restrict__ phase, int *__restrict__ pos, int *counter) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const bool alive = m < A && phase[m] == PH_ITER;
+  const bool alive = m < A && phase[m] != PH_DONE;
   const unsigned mask = __ballot_sync(0xffffffffu, alive);
   int base = 0;
   if (mask) {
@@ -560,9 +903,11 @@ __global__ void k_repack_pos(int A, const int *__restrict__ phase, int *__restri
   if (m < A) pos[m] = alive ? base + __popc(mask & ((1u << lane) - 1u)) : -1;
 }
 
-// Copies rows [0, rows) of a [rows][ld] array for every slot that moves.
-__global__ void k_repack_rows(int A, int ld, long long rows, const int *__restrict__ pos,
-                              const double *__restrict__ src, double *__restrict__ dst) {
+// Copies rows [0, rows) of a [rows][ld] array (T = double or float) for every
+// slot that moves.
+template <typename T>
+__global__ void k_repack_rows(int A, int ld, long long rows, const int *__restrict__ pos, const T *__restrict__ src,
+                              T *__restrict__ dst) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= A) return;
   const int d = pos[m];
@@ -570,41 +915,48 @@ __global__ void k_repack_rows(int A, int ld, long long rows, const int *__restri
   for (long long r = blockIdx.y; r < rows; r += gridDim.y) dst[(size_t)r * ld + d] = src[(size_t)r * ld + m];
 }
 
+// Moves the control state and rebuilds the lists the next round reads.  The
+// block size is a multiple of 32 and every lane reaches the list append.
 __global__ void k_repack_ctl(Sweep s, Ctl a, Ctl b, const int *__restrict__ pos) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= s.A) return;
-  const int d = pos[m];
-  if (d < 0) return;
-  const int ld = s.ld;
-  for (int q = 0; q < 6; q++) b.x[q * ld + d] = a.x[q * ld + m];
-  b.hbase[d] = a.hbase[m];
-  b.ta[d] = a.ta[m];
-  b.tb[d] = a.tb[m];
-  b.w1[d] = a.w1[m];
-  b.w2[d] = a.w2[m];
-  b.e_best[d] = a.e_best[m];
-  b.err[d] = a.err[m];
-  b.p[d] = a.p[m];
-  b.depth[d] = a.depth[m];
-  b.phase[d] = a.phase[m];
-  b.status[d] = a.status[m];
-  b.sweeps[d] = a.sweeps[m];
-  b.seg_sweeps[d] = a.seg_sweeps[m];
-  b.nstall[d] = a.nstall[m];
-  b.nseg[d] = a.nseg[m];
-  b.need_setup[d] = a.need_setup[m];
-  b.last[d] = a.last[m];
-  b.ic[d] = a.ic[m];
-  if (a.need_setup[m]) {
-    const int k = atomicAdd(s.list_cnt + s.list_cur, 1);
-    s.list[s.list_cur][k] = d;
+  const int d = (m < s.A) ? pos[m] : -1;
+  const int list_next = s.list_cur;  // the list the next round reads
+  bool to64 = false;
+  if (d >= 0) {
+    const int ld = s.ld;
+    for (int q = 0; q < 6; q++) b.x[q * ld + d] = a.x[q * ld + m];
+    b.hbase[d] = a.hbase[m];
+    b.ta[d] = a.ta[m];
+    b.tb[d] = a.tb[m];
+    b.w1[d] = a.w1[m];
+    b.w2[d] = a.w2[m];
+    b.e_best[d] = a.e_best[m];
+    b.err[d] = a.err[m];
+    b.p[d] = a.p[m];
+    b.depth[d] = a.depth[m];
+    b.phase[d] = a.phase[m];
+    b.status[d] = a.status[m];
+    b.sweeps[d] = a.sweeps[m];
+    b.seg_sweeps[d] = a.seg_sweeps[m];
+    b.nstall[d] = a.nstall[m];
+    b.nseg[d] = a.nseg[m];
+    b.need_setup[d] = a.need_setup[m];
+    b.last[d] = a.last[m];
+    b.ic[d] = a.ic[m];
+    b.err32[d] = a.err32[m];
+    if (a.need_setup[m]) {
+      const int k = atomicAdd(s.list_cnt + list_next, 1);
+      s.list[list_next][k] = d;
+    }
+    to64 = a.phase[m] == PH_ITER;
   }
+  warp_append(to64, d, s.l64[list_next], s.l64_cnt + list_next);
 }
 
 // Round cap reached: remaining trajectories stop with NOT_CONVERGED.
 __global__ void k_abort(Sweep s, Ctl c) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= s.A || c.phase[m] != PH_ITER) return;
+  if (m >= s.A || c.phase[m] == PH_DONE) return;
   c.status[m] |= PC_IC_NOT_CONVERGED;
   c.phase[m] = PH_DONE;
   write_outputs(s, c, m);
@@ -614,9 +966,10 @@ __global__ void k_abort(Sweep s, Ctl c) {
 __global__ void k_eval_ephem(Model md, long long n, const double *__restrict__ t, double *__restrict__ rb) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const EphemLoc L = ephem_locate(md, t[i]);
   for (int b = 0; b < md.B; b++) {
     double r[3];
-    ephem_at(md, t[i], b, r);
+    ephem_body(md, L, b, r);
     for (int ax = 0; ax < 3; ax++) rb[(size_t)(b * 3 + ax) * n + i] = r[ax];
   }
 }
@@ -637,8 +990,9 @@ __global__ void k_eval_dyn(Model md, long long n, const double *__restrict__ t, 
   if (i >= n) return;
   double rb[kMaxBodies * 3];
   double ind[3] = {0.0, 0.0, 0.0};
+  const EphemLoc L = ephem_locate(md, t[i]);
   for (int b = 0; b < md.B; b++) {
-    ephem_at(md, t[i], b, rb + 3 * b);
+    ephem_body(md, L, b, rb + 3 * b);
     if (md.indirect) add_indirect(md, b, rb + 3 * b, ind);
   }
   const double r[3] = {y[i], y[n + i], y[2 * n + i]};
@@ -654,13 +1008,42 @@ constexpr int kThreads = 128;
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+Mix live_mix(const pc_plan *p) {
+  const Workspace &w = p->ws;
+  Mix mx{};
+  mx.YK = w.YK;
+  mx.X32 = w.X32;
+  mx.xs = x32_stride(p->model.B);
+  return mx;
+}
+
+// The FP32 operator goes to shared memory when it fits beside the force tables.
+constexpr size_t kFp32KsmemLimit = 120 * 1024;
+
+template <int NPL>
+void launch_fp32(const pc_plan *p, const Sweep &s, double *Y, const Mix &mx, cudaStream_t st) {
+  const size_t k_bytes = (size_t)p->n * 32 * NPL * sizeof(float);
+  const size_t g_bytes = (size_t)kFp32Warps * p->n * 6 * sizeof(float);
+  const Ctl &c = p->ws.ctl[p->ws.live];
+  if (k_bytes + g_bytes <= kFp32KsmemLimit) {
+    cudaFuncSetAttribute(k_fp32<NPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k_bytes + g_bytes));
+    k_fp32<NPL, true><<<152 * 2, 32 * kFp32Warps, k_bytes + g_bytes, st>>>(s, c, p->model, p->d_K32T, p->d_mu32, Y,
+                                                                          mx);
+  } else {
+    cudaFuncSetAttribute(k_fp32<NPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_bytes);
+    k_fp32<NPL, false><<<152 * 2, 32 * kFp32Warps, g_bytes, st>>>(s, c, p->model, p->d_K32T, p->d_mu32, Y, mx);
+  }
+}
+
 }  // namespace
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cudaStream_t st) {
   const Workspace &w = p->ws;
-  cudaError_t e = cudaMemsetAsync(w.ints, 0, 8 * sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(w.ints, 0, 16 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.cnt64, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  p->acc_launches += 1;
   k_init<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, w.ctl[w.live], p->model, x0, w.ints);
   return cudaGetLastError();
 }
@@ -671,17 +1054,34 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   const Ctl &c = w.ctl[w.live];
   double *Yc = w.Y[cur], *Yn = w.Y[cur ^ 1];
   double *E = w.E[w.live], *Ai = w.Aind[w.live];
+  const Mix mx = live_mix(p);
   if (ev) cudaEventRecord(ev[0], st);
-  k_setup<<<152 * 4, kThreads, 0, st>>>(s, c, p->model, p->d_tau, Yc, E, Ai);
+  k_setup<<<152 * 4, kThreads, 0, st>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
   if (ev) cudaEventRecord(ev[1], st);
-  const dim3 gnode(blocks_for(s.A, kThreads), s.n);
-  k_force<<<gnode, kThreads, 0, st>>>(s, c, p->model, Yc, E, Ai, w.G);
+  if (s.mixed) {
+    switch (p->npl) {
+      case 1: launch_fp32<1>(p, s, Yc, mx, st); break;
+      case 2: launch_fp32<2>(p, s, Yc, mx, st); break;
+      case 3: launch_fp32<3>(p, s, Yc, mx, st); break;
+      case 4: launch_fp32<4>(p, s, Yc, mx, st); break;
+      case 5: launch_fp32<5>(p, s, Yc, mx, st); break;
+      case 6: launch_fp32<6>(p, s, Yc, mx, st); break;
+      case 7: launch_fp32<7>(p, s, Yc, mx, st); break;
+      case 8: launch_fp32<8>(p, s, Yc, mx, st); break;
+      default: launch_fp32<9>(p, s, Yc, mx, st); break;
+    }
+  }
   if (ev) cudaEventRecord(ev[2], st);
-  const long long warps = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
-  k_contract<false><<<blocks_for(warps * 32, 256), 256, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn);
+  k_force<<<dim3(blocks_for(s.A, kThreads), s.n), kThreads, 0, st>>>(s, c, p->model, Yc, E, Ai, w.G);
   if (ev) cudaEventRecord(ev[3], st);
-  k_control<<<blocks_for(s.A, kThreads), kThreads, 0, st>>>(s, c, p->d_tau, w.G, Yn, w.ints);
+  // persistent FP64 contraction: 4 CTAs of kSplit warps per SM
+  const long long tiles = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
+  const long long blocks = std::min<long long>(152 * 4, tiles);
+  k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn);
   if (ev) cudaEventRecord(ev[4], st);
+  k_control<<<blocks_for(s.A, kThreads), kThreads, 0, st>>>(s, c, p->d_tau, w.G, Yn, w.ints);
+  if (ev) cudaEventRecord(ev[5], st);
+  p->acc_launches += s.mixed ? 5 : 4;
   return cudaGetLastError();
 }
 
@@ -691,20 +1091,24 @@ cudaError_t launch_repack(const pc_plan *p, const Sweep &s, int cur, cudaStream_
   const int a = w.live, b = w.live ^ 1;
   cudaError_t e = cudaMemsetAsync(w.ints + 4, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.list_cnt + s.list_cur, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.l64_cnt + s.list_cur, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   const unsigned nb = blocks_for(s.A, kThreads);
   k_repack_pos<<<nb, kThreads, 0, st>>>(s.A, w.ctl[a].phase, w.pos, w.ints + 4);
   const long long n = p->n, B = p->model.B;
-  k_repack_rows<<<dim3(nb, 64), kThreads, 0, st>>>(s.A, s.ld, n * 6, w.pos, w.Y[cur], w.Y[cur ^ 1]);
-  if (B > 0) k_repack_rows<<<dim3(nb, 64), kThreads, 0, st>>>(s.A, s.ld, n * B * 3, w.pos, w.E[a], w.E[b]);
-  k_repack_rows<<<dim3(nb, 64), kThreads, 0, st>>>(s.A, s.ld, n * 3, w.pos, w.Aind[a], w.Aind[b]);
+  const dim3 g(nb, 64);
+  k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 6, w.pos, w.Y[cur], w.Y[cur ^ 1]);
+  if (B > 0) k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * B * 3, w.pos, w.E[a], w.E[b]);
+  k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 3, w.pos, w.Aind[a], w.Aind[b]);
   k_repack_ctl<<<nb, kThreads, 0, st>>>(s, w.ctl[a], w.ctl[b], w.pos);
+  p->acc_launches += 4 + (B > 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_abort(const pc_plan *p, const Sweep &s, cudaStream_t st) {
   if (s.A <= 0) return cudaSuccess;
   k_abort<<<blocks_for(s.A, kThreads), kThreads, 0, st>>>(s, p->ws.ctl[p->ws.live]);
+  p->acc_launches += 1;
   return cudaGetLastError();
 }
 
@@ -739,8 +1143,8 @@ cudaError_t launch_apply_operator(const pc_plan *p, long long n_ic, int ld, cons
   s.ld = ld;
   Ctl c = w.ctl[w.live];
   c.x = const_cast<double *>(x0);
-  const long long warps = (long long)(s.rows_pad / 16) * (s.ld / 8);
-  k_contract<true><<<blocks_for(warps * 32, 256), 256, 0, st>>>(s, c, p->d_K, G, nullptr, Y);
+  const long long tiles = (long long)(s.rows_pad / 16) * ((n_ic + 7) / 8);
+  k_contract_diag<<<(unsigned)std::min<long long>(tiles, 152 * 8), 32 * kSplit, 0, st>>>(s, c, p->d_K, G, Y);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ PC_PREC_FP64, PC_PREC_MIXED = 0, 1
 EXPORTS = ["pc_options_default", "pc_plan_create", "pc_propagate", "pc_propagate_ex", "pc_eval_ephemeris",
            "pc_eval_dynamics", "pc_eval_warm_start", "pc_apply_operator", "pc_plan_operator", "pc_plan_destroy",
            "pc_status_string", "pc_plan_set_profiling", "pc_plan_kernel_times", "pc_apply_operator_static"]
-KERNEL_NAMES = ["setup", "force", "contract", "control"]
+KERNEL_NAMES = ["setup", "fp32", "force", "contract", "control"]
 
 
 class PCError(RuntimeError):
@@ -45,7 +45,8 @@ class Ephemeris(C.Structure):
 
 
 class KernelTimes(C.Structure):
-    _fields_ = [("launches", C.c_longlong * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_longlong * 5), ("ms", C.c_double * 5), ("sweeps64", C.c_longlong),
+                ("sweeps32", C.c_longlong), ("kernel_launches", C.c_longlong)]
 
 
 class Options(C.Structure):
@@ -231,7 +232,13 @@ def set_profiling(plan: Plan, on: bool = True):
 
 
 def kernel_times(plan: Plan) -> dict:
-    """{kernel: (launches, summed ms)} recorded since the last call."""
+    """{kernel: (launch records, summed ms)} recorded since the last call, plus
+    'sweeps64', 'sweeps32' (trajectory-sweeps per precision) and
+    'kernel_launches' (device kernels launched)."""
     kt = KernelTimes()
     _check(lib().pc_plan_kernel_times(plan.handle, C.byref(kt)), "pc_plan_kernel_times")
-    return {name: (int(kt.launches[k]), float(kt.ms[k])) for k, name in enumerate(KERNEL_NAMES)}
+    out = {name: (int(kt.launches[k]), float(kt.ms[k])) for k, name in enumerate(KERNEL_NAMES)}
+    out["sweeps64"] = int(kt.sweeps64)
+    out["sweeps32"] = int(kt.sweeps32)
+    out["kernel_launches"] = int(kt.kernel_launches)
+    return out
