@@ -429,18 +429,26 @@ static int ora_pc_segment_core(const ora_model *m, const ora_opts *o, const doub
       double ej = dr > dv ? dr : dv;
       if (!(ej <= e)) e = ej; /* propagates NaN */
     }
+    int out = -1;
+    if (!(e <= o->div_limit)) {
+      out = ORA_SEG_FAIL_DIV;
+    } else if (e < o->tol) {
+      out = ORA_SEG_OK;
+    } else {
+      if (e < e_best) { e_best = e; nstall = 0; } else { nstall++; }
+      if (nstall >= o->stall_sweeps && e_best < o->stall_factor * o->tol) out = ORA_SEG_STALLED;
+    }
+    /* resolution test on an accepted segment: the force table of this sweep
+       against the norms of the iterate it was evaluated on (Y, not yet updated) */
+    if ((out == ORA_SEG_OK || out == ORA_SEG_STALLED) && o->trunc_tol > 0.0 &&
+        !(ora_tail(o, G, Y, N, tau, w2) <= o->trunc_tol))
+      out = ORA_SEG_FAIL_TRUNC;
     memcpy(Y, Ynew, sizeof(double) * 6 * n);
-    if (!(e <= o->div_limit)) { outcome = ORA_SEG_FAIL_DIV; break; }
-    if (e < o->tol) { outcome = ORA_SEG_OK; break; }
-    if (e < e_best) { e_best = e; nstall = 0; } else { nstall++; }
-    if (nstall >= o->stall_sweeps && e_best < o->stall_factor * o->tol) { outcome = ORA_SEG_STALLED; break; }
+    if (out >= 0) { outcome = out; break; }
   }
   if (i > o->max_iters) i = o->max_iters;
   if (iters_out) *iters_out = i;
   if (err_out) *err_out = e;
-  if ((outcome == ORA_SEG_OK || outcome == ORA_SEG_STALLED) && o->trunc_tol > 0.0 &&
-      ora_tail(o, G, Y, N, tau, w2) > o->trunc_tol)
-    outcome = ORA_SEG_FAIL_TRUNC;
   return outcome;
 }
 
