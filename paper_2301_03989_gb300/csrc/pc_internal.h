@@ -83,6 +83,7 @@ struct Workspace {
   int ld = 0;
   double *Y[2] = {nullptr, nullptr};  // [n][6][ld] FP64 iterate (current / next; also repack target)
   double *G = nullptr;       // [kpad][6][ld]; rows n..kpad-1 stay zero
+  double *tails = nullptr;   // [ceil(n/8)][14][ld] resolution-test partial sums of the round's FP64 sweeps
   double *E[2] = {nullptr, nullptr};    // [n][B][3][ld] body positions at the nodes (+ repack target)
   double *Aind[2] = {nullptr, nullptr}; // [n][3][ld] summed indirect acceleration (+ repack target)
   // mixed precision (allocated when the plan asks for it), by new-segment list entry

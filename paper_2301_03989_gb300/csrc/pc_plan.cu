@@ -226,6 +226,7 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic, int mixed) {
   for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc(&w.Y[b], n * 6 * ld);
   if (e == cudaSuccess) e = dalloc(&w.G, kpad * 6 * ld);
   if (e == cudaSuccess) e = cudaMemset(w.G, 0, sizeof(double) * kpad * 6 * ld);
+  if (e == cudaSuccess) e = dalloc(&w.tails, (n + 7) / 8 * 14 * ld);
   const size_t ctl_bytes = (size_t)ld * (kCtlDoubles * 8 + 8 + 8 + kCtlInts * 4) + 256;
   for (int b = 0; b < 2 && e == cudaSuccess; b++) {
     if (B > 0) e = dalloc(&w.E[b], n * B * 3 * ld);
@@ -269,6 +270,7 @@ void pcx::free_workspace(pc_plan *p) {
   cudaFree(w.YK);
   cudaFree(w.X32);
   cudaFree(w.G);
+  cudaFree(w.tails);
   cudaFree(w.lists);
   cudaFree(w.pos);
   cudaFree(w.ints);

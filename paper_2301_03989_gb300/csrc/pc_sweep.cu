@@ -187,11 +187,14 @@ __device__ __forceinline__ void ephem_body(const Model &md, EphemLoc L, int b, d
 // ---------------------------------------------------------------------------
 // Keplerian two-body propagation by dt (warm start).  Kepler's equation in the
 // eccentric-anomaly increment X over dt,
-//   n dt = X - (e cos E0) sin X + (e sin E0)(1 - cos X),
+//   F(X) = X - (e cos E0) sin X + (e sin E0)(1 - cos X) - n dt = 0,
 // with e cos E0 = 1 - r0/a and e sin E0 = r0.v0/sqrt(mu a), is solved by
-// Newton's method kept inside the bracket [n dt - 2, n dt + 2], then the
-// Lagrange coefficients map (r0, v0) to (r, v).  Returns false if the orbit
-// is not a bound ellipse or Newton does not settle.
+// Halley's method (third order: X <- X - 2 F F' / (2 F'^2 - F F'')), kept
+// inside the bracket [n dt - 2, n dt + 2] by bisection.  Once a step is below
+// 1e-6 the cubic convergence puts the next error below 1e-17 and the iteration
+// stops after applying it.  The Lagrange coefficients then map (r0, v0) to
+// (r, v).  Returns false if the orbit is not a bound ellipse or the iteration
+// does not settle.
 // ---------------------------------------------------------------------------
 __device__ bool kepler_dt(double mu, const double x0[6], double dt, double out[6]) {
   const double r0 = sqrt(x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2]);
@@ -213,12 +216,14 @@ __device__ bool kepler_dt(double mu, const double x0[6], double dt, double out[6
     sincos(X, &sX, &cX);
     const double F = X - ecE * sX + esE * (1.0 - cX) - M;
     if (F > 0.0) hi = X; else lo = X;
-    const double dF = 1.0 - ecE * cX + esE * sX;
-    double Xn = X - F / dF;
-    if (!(Xn > lo && Xn < hi)) Xn = 0.5 * (lo + hi);
+    const double d1 = 1.0 - ecE * cX + esE * sX;
+    const double d2 = ecE * sX + esE * cX;
+    double Xn = X - 2.0 * F * d1 / (2.0 * d1 * d1 - F * d2);
+    const bool halley = Xn > lo && Xn < hi;
+    if (!halley) Xn = 0.5 * (lo + hi);
     const double step = fabs(Xn - X);
     X = Xn;
-    if (step <= 1e-15 * (1.0 + fabs(X))) { ok = true; break; }
+    if ((halley && step <= 1e-6 * (1.0 + fabs(X))) || step <= 1e-15 * (1.0 + fabs(X))) { ok = true; break; }
   }
   if (!ok) return false;
   double sX, cX;
@@ -352,26 +357,70 @@ __device__ __forceinline__ void accel(const Model &md, const double *__restrict_
   }
 }
 
-__global__ void k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y, const double *__restrict__ E,
-                        const double *__restrict__ Aind, double *__restrict__ G) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (i >= s.l64_cnt[s.list_cur]) return;
-  const int m = s.l64[s.list_cur][i];
-  const int ld = s.ld;
-  const double w2 = c.w2[m];
-  const size_t yb = (size_t)j * 6 * ld + m;
-  double y[6];
+// Resolution-test sums, accumulated while the force table is built (see the
+// resolution test below): per trajectory, for each component q,
+//   sN[q]  = sum''_j (-1)^(N+j) F_j[q],   sN1[q] = sum''_j (-1)^(N+j) tau_j F_j[q]
+// and the largest |r_j|^2, |v_j|^2 of the iterate.  Each block sums its
+// kForceNodes nodes in node order into partials[nb][v][slot] (node block nb;
+// v = 0..5 sN, 6..11 sN1, 12 max|r|^2, 13 max|v|^2); the control kernel adds
+// the node blocks in order.  The sums never depend on scheduling.
+constexpr int kTailVals = 14;
+constexpr int kForceNodes = 8;
+
+// Block = 32 FP64-list entries (x) by kForceNodes nodes (y); one thread per
+// (entry, node).
+__global__ void __launch_bounds__(32 * kForceNodes) k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y,
+                                                          const double *__restrict__ E,
+                                                          const double *__restrict__ Aind, double *__restrict__ G,
+                                                          const double *__restrict__ tau,
+                                                          double *__restrict__ partials) {
+  __shared__ double red[kForceNodes][kTailVals][32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * 32 + tx;
+  const int j = blockIdx.y * kForceNodes + ty;
+  const int count = s.l64_cnt[s.list_cur];
+  const bool valid = i < count;
+  const int m = valid ? s.l64[s.list_cur][i] : 0;
+  const int ld = s.ld, N = s.N;
+  double acc[kTailVals];
 #pragma unroll
-  for (int q = 0; q < 6; q++) y[q] = Y[yb + (size_t)q * ld];
-  double a[3];
-  accel(md, E + (size_t)j * md.B * 3 * ld + m, Aind + (size_t)j * 3 * ld + m, (size_t)ld, y, a);
-  G[yb] = w2 * y[3];
-  G[yb + ld] = w2 * y[4];
-  G[yb + 2 * (size_t)ld] = w2 * y[5];
-  G[yb + 3 * (size_t)ld] = w2 * a[0];
-  G[yb + 4 * (size_t)ld] = w2 * a[1];
-  G[yb + 5 * (size_t)ld] = w2 * a[2];
+  for (int v = 0; v < kTailVals; v++) acc[v] = 0.0;
+  if (valid && j <= N) {
+    const double w2 = c.w2[m];
+    const size_t yb = (size_t)j * 6 * ld + m;
+    double y[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) y[q] = Y[yb + (size_t)q * ld];
+    double a[3];
+    accel(md, E + (size_t)j * md.B * 3 * ld + m, Aind + (size_t)j * 3 * ld + m, (size_t)ld, y, a);
+    const double g[6] = {w2 * y[3], w2 * y[4], w2 * y[5], w2 * a[0], w2 * a[1], w2 * a[2]};
+#pragma unroll
+    for (int q = 0; q < 6; q++) G[yb + (size_t)q * ld] = g[q];
+    const double wj = (j == 0 || j == N) ? 0.5 : 1.0;
+    const double sg = ((N + j) & 1) ? -wj : wj;
+    const double st = sg * tau[j];
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      acc[q] = sg * g[q];
+      acc[6 + q] = st * g[q];
+    }
+    acc[12] = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    acc[13] = y[3] * y[3] + y[4] * y[4] + y[5] * y[5];
+  }
+#pragma unroll
+  for (int v = 0; v < kTailVals; v++) red[ty][v][tx] = acc[v];
+  __syncthreads();
+  if (ty == 0 && valid) {
+    for (int u = 1; u < kForceNodes; u++) {
+#pragma unroll
+      for (int v = 0; v < 12; v++) acc[v] += red[u][v][tx];
+      acc[12] = fmax(acc[12], red[u][12][tx]);
+      acc[13] = fmax(acc[13], red[u][13][tx]);
+    }
+    double *pp = partials + (size_t)blockIdx.y * kTailVals * ld + m;
+#pragma unroll
+    for (int v = 0; v < kTailVals; v++) pp[(size_t)v * ld] = acc[v];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -562,12 +611,13 @@ __global__ void __launch_bounds__(32 * kSplit) k_contract_diag(Sweep s, Ctl c, c
 // rows of the contraction, so the deviation stays in registers across sweeps;
 // the warp's force table F32[j][6] is shared through shared memory, and the
 // block stages the FP32 operator K32T ([N+1][32 NPL], transposed) in shared
-// memory when KSMEM.  The sweeps stop when the change is below switch_tol,
-// fails to halve the best change for two sweeps (the FP32 floor) or reaches
+// memory when KSMEM.  The sweeps stop when the change is below switch_tol or
+// the FP32 floor, fails to halve the best change for two sweeps, or reaches
 // max_iters: then Y = y_K + delta is written and the trajectory joins this
 // round's FP64 list.  A non-finite or huge change leaves the trajectory in the
 // FP32 phase with that change, and the control kernel halves the segment.
 constexpr int kFp32Warps = 8;
+constexpr float kFp32Floor = 2e-6f;
 
 template <int NPL, bool KSMEM>
 __global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model md, const float *__restrict__ K32T,
@@ -577,20 +627,35 @@ __global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model 
   float *sm = reinterpret_cast<float *>(fp32_smem4);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int N = s.N, n = s.n, ld = s.ld, B = md.B, np = 32 * NPL;
+  // With KSMEM the operator is staged per lane: Ks[l * lstride + i * n4 + k] =
+  // K[l + 32 i][k], k padded to n4 = 4 ceil(n/4) with zeros, and
+  // lstride = 32 ceil(NPL n4 / 32) + 4 so that the 16-byte loads of 8
+  // consecutive lanes hit distinct bank groups.  Each lane then reads four
+  // k-values of a row with one 16-byte load.
+  const int n4 = (n + 3) & ~3;
+  const int lstride = ((NPL * n4 + 31) & ~31) + 4;
   const float *Kt = K32T;
   float *Gs;
   if (KSMEM) {
     float *Ks = sm;
-    for (int i = threadIdx.x; i < n * np; i += blockDim.x) Ks[i] = K32T[i];
-    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * NPL * n4; idx += blockDim.x) {
+      const int k = idx % n4, li = idx / n4;  // li = l * NPL + i
+      const int l = li / NPL, i = li % NPL;
+      Ks[l * lstride + i * n4 + k] = (k < n) ? K32T[(size_t)k * np + l + 32 * i] : 0.0f;
+    }
     Kt = Ks;
-    Gs = sm + (size_t)n * np + (size_t)wib * n * 6;
+    Gs = sm + (size_t)32 * lstride + (size_t)wib * n4 * 6;
+    for (int k = n + lane; k < n4; k += 32)
+      for (int q = 0; q < 6; q++) Gs[k * 6 + q] = 0.0f;
+    __syncthreads();
   } else {
     Gs = sm + (size_t)wib * n * 6;
   }
   const int cur = s.list_cur;
   const int count = s.list_cnt[cur];
-  for (int e = blockIdx.x * kFp32Warps + wib; e < count; e += gridDim.x * kFp32Warps) {
+  // entries go to blocks first (e = wib * gridDim.x + blockIdx.x), so a round
+  // with few new segments still spreads them over every SM
+  for (int e = wib * gridDim.x + blockIdx.x; e < count; e += gridDim.x * kFp32Warps) {
     const int m = s.list[cur][e];
     const float w2f = (float)c.w2[m];
     const float *recs = mx.X32 + (size_t)e * n * mx.xs;
@@ -645,21 +710,48 @@ __global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model 
       for (int i = 0; i < NPL; i++)
 #pragma unroll
         for (int q = 0; q < 6; q++) acc[i][q] = 0.0f;
+      if (KSMEM) {
+        const float *kl = Kt + (size_t)lane * lstride;
+        for (int k = 0; k < n4; k += 4) {
+          float4 kv[NPL];
+#pragma unroll
+          for (int i = 0; i < NPL; i++) kv[i] = *reinterpret_cast<const float4 *>(kl + i * n4 + k);
+          const float4 *g4 = reinterpret_cast<const float4 *>(Gs + k * 6);
+          float g[24];
+#pragma unroll
+          for (int v = 0; v < 6; v++) {
+            const float4 t4 = g4[v];
+            g[4 * v] = t4.x;
+            g[4 * v + 1] = t4.y;
+            g[4 * v + 2] = t4.z;
+            g[4 * v + 3] = t4.w;
+          }
+#pragma unroll
+          for (int i = 0; i < NPL; i++) {
+            const float kk[4] = {kv[i].x, kv[i].y, kv[i].z, kv[i].w};
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+              for (int q = 0; q < 6; q++) acc[i][q] = fmaf(kk[u], g[6 * u + q], acc[i][q]);
+          }
+        }
+      } else {
 #pragma unroll 2
-      for (int k = 0; k < n; k++) {
-        const float2 *g2 = reinterpret_cast<const float2 *>(Gs + k * 6);
-        const float2 ga = g2[0], gb = g2[1], gc = g2[2];
-        const float g[6] = {ga.x, ga.y, gb.x, gb.y, gc.x, gc.y};
-        const float *kr = Kt + (size_t)k * np + lane;
+        for (int k = 0; k < n; k++) {
+          const float2 *g2 = reinterpret_cast<const float2 *>(Gs + k * 6);
+          const float2 ga = g2[0], gb = g2[1], gc = g2[2];
+          const float g[6] = {ga.x, ga.y, gb.x, gb.y, gc.x, gc.y};
+          const float *kr = Kt + (size_t)k * np + lane;
 #pragma unroll
-        for (int i = 0; i < NPL; i++) {
-          const float kv = KSMEM ? kr[32 * i] : __ldg(kr + 32 * i);
+          for (int i = 0; i < NPL; i++) {
+            const float kv = __ldg(kr + 32 * i);
 #pragma unroll
-          for (int q = 0; q < 6; q++) acc[i][q] = fmaf(kv, g[q], acc[i][q]);
+            for (int q = 0; q < 6; q++) acc[i][q] = fmaf(kv, g[q], acc[i][q]);
+          }
         }
       }
       __syncwarp();
-      float emax = 0.0f;
+      float emax = 0.0f, dmax = 0.0f;
 #pragma unroll
       for (int i = 0; i < NPL; i++) {
         const int j = lane + 32 * i;
@@ -676,31 +768,39 @@ __global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model 
         }
         float dr = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         float dv = sqrtf(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+        float mr = sqrtf(acc[i][0] * acc[i][0] + acc[i][1] * acc[i][1] + acc[i][2] * acc[i][2]);
+        float mv = sqrtf(acc[i][3] * acc[i][3] + acc[i][4] * acc[i][4] + acc[i][5] * acc[i][5]);
         if (s.relative) {
           const float nr = sqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
           const float nv = sqrtf(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
-          if (nr > 0.0f) dr /= nr;
-          if (nv > 0.0f) dv /= nv;
+          if (nr > 0.0f) { dr /= nr; mr /= nr; }
+          if (nv > 0.0f) { dv /= nv; mv /= nv; }
         }
         emax = nanmaxf(emax, nanmaxf(dr, dv));
+        dmax = fmaxf(dmax, fmaxf(mr, mv));
       }
 #pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) emax = nanmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      for (int o = 16; o >= 1; o >>= 1) {
+        emax = nanmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      }
       it++;
       efin = emax;
       if (!((double)emax <= s.div_limit)) {
         fail = true;
         break;
       }
-      // progress = at least halving the best change so far; at the FP32 floor
-      // the change only fluctuates, and two sweeps without progress end the phase
+      // The FP32 floor: the change cannot fall much below the rounding of the
+      // contraction, ~sqrt(N) FP32 ulps of the deviation itself, so a change
+      // under kFp32Floor * max|delta|/|y| ends the phase.  Failing to halve the
+      // best change for two sweeps (fluctuation at the floor) also ends it.
       if (emax < 0.5f * ebest) {
         nst = 0;
       } else {
         nst++;
       }
       ebest = fminf(ebest, emax);
-      if ((double)emax < s.switch_tol || nst >= 2 || it >= s.max_iters) break;
+      if ((double)emax < s.switch_tol || emax < kFp32Floor * dmax || nst >= 2 || it >= s.max_iters) break;
     }
     if (!fail) {
 #pragma unroll
@@ -735,54 +835,35 @@ __global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model 
 // T_N(tau_j) = (-1)^(N+j) and T_{N-1}(tau_j) = (-1)^(N+j) tau_j, so the two
 // top coefficients of the interpolant of g are
 //   a_N = (1/N) sum''_j (-1)^(N+j) g_j,   a_{N-1} = (2/N) sum''_j (-1)^(N+j) tau_j g_j
-// (sum'' halves the end terms).  The integrated error is about
-// 2 |omega2| (|a_{N-1}| + |a_N|) per unit of g; F already carries omega2.
-// Position components are measured against max_j |r_j|, velocity ones against
-// max_j |v_j| (relative mode).  Warp-cooperative: lanes split the nodes of slot
-// m, the sums are reduced across the warp and every lane returns the estimate.
+// (sum'' halves the end terms; the sums come from k_force).  The integrated
+// error is about 2 |omega2| (|a_{N-1}| + |a_N|) per unit of g; F already
+// carries omega2.  Position components are measured against max_j |r_j|,
+// velocity ones against max_j |v_j| of the iterate the force was evaluated on
+// (relative mode).
 // ---------------------------------------------------------------------------
-__device__ double warp_tail_estimate(const Sweep &s, const double *__restrict__ tau, const double *__restrict__ G,
-                                     const double *__restrict__ Y, int m) {
-  const int ld = s.ld, N = s.N, lane = threadIdx.x & 31;
-  double sN[6] = {0, 0, 0, 0, 0, 0}, sN1[6] = {0, 0, 0, 0, 0, 0};
-  double rmax = 0.0, vmax = 0.0;
-  for (int j = lane; j <= N; j += 32) {
-    const double w = (j == 0 || j == N) ? 0.5 : 1.0;
-    const double sg = ((N + j) & 1) ? -w : w;
-    const double tj = tau[j] * sg;
-    const size_t base = (size_t)j * 6 * ld + m;
+__device__ double tail_estimate(const Sweep &s, const double *__restrict__ partials, int m) {
+  const int ld = s.ld;
+  const int nb = (s.n + kForceNodes - 1) / kForceNodes;
+  double sums[12], r2 = 0.0, v2 = 0.0;
 #pragma unroll
-    for (int q = 0; q < 6; q++) {
-      const double gq = G[base + (size_t)q * ld];
-      sN[q] = fma(sg, gq, sN[q]);
-      sN1[q] = fma(tj, gq, sN1[q]);
-    }
-    if (s.relative) {
-      const double y0 = Y[base], y1 = Y[base + ld], y2 = Y[base + 2 * (size_t)ld];
-      const double y3 = Y[base + 3 * (size_t)ld], y4 = Y[base + 4 * (size_t)ld], y5 = Y[base + 5 * (size_t)ld];
-      rmax = fmax(rmax, sqrt(y0 * y0 + y1 * y1 + y2 * y2));
-      vmax = fmax(vmax, sqrt(y3 * y3 + y4 * y4 + y5 * y5));
-    }
+  for (int v = 0; v < 12; v++) sums[v] = 0.0;
+  for (int b = 0; b < nb; b++) {
+    const double *pp = partials + (size_t)b * kTailVals * ld + m;
+#pragma unroll
+    for (int v = 0; v < 12; v++) sums[v] += pp[(size_t)v * ld];
+    r2 = fmax(r2, pp[(size_t)12 * ld]);
+    v2 = fmax(v2, pp[(size_t)13 * ld]);
   }
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-      sN[q] += __shfl_xor_sync(0xffffffffu, sN[q], o);
-      sN1[q] += __shfl_xor_sync(0xffffffffu, sN1[q], o);
-    }
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-  }
+  const double invN = 1.0 / (double)s.N;
   double er = 0.0, ev = 0.0;
 #pragma unroll
   for (int q = 0; q < 6; q++) {
-    const double tl = 2.0 * (fabs(2.0 * sN1[q] / N) + fabs(sN[q] / N));
+    const double tl = 2.0 * (fabs(2.0 * sums[6 + q] * invN) + fabs(sums[q] * invN));
     if (q < 3) er = nanmax(er, tl); else ev = nanmax(ev, tl);
   }
   if (s.relative) {
-    if (rmax > 0.0) er /= rmax;
-    if (vmax > 0.0) ev /= vmax;
+    if (r2 > 0.0) er /= sqrt(r2);
+    if (v2 > 0.0) ev /= sqrt(v2);
   }
   return nanmax(er, ev);
 }
@@ -793,8 +874,8 @@ __device__ double warp_tail_estimate(const Sweep &s, const double *__restrict__ 
 // failed it (blow-up) and is halved.  Finished trajectories write their outputs.  Trajectories doing an FP64 sweep next
 // round go on the next FP64 list.  The block size is a multiple of 32 and every
 // lane reaches the warp-cooperative steps.
-__global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const double *__restrict__ G,
-                          const double *__restrict__ Ynew, int *done) {
+__global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, const double *__restrict__ Ynew,
+                          int *done) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int phase = (m < s.A) ? c.phase[m] : PH_DONE;
@@ -833,18 +914,9 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tau, const 
       out = SEG_FAIL_DIV;
     }
   }
-  const bool want_tail = act && (out == SEG_OK || out == SEG_STALLED) && s.trunc_tol > 0.0;
-  unsigned pending = __ballot_sync(0xffffffffu, want_tail);
-  double my_tail = 0.0;
-  while (pending) {
-    const int b = __ffs(pending) - 1;
-    pending &= pending - 1;
-    const int mb = __shfl_sync(0xffffffffu, m, b);
-    const double tl = warp_tail_estimate(s, tau, G, Ynew, mb);
-    if (lane == b) my_tail = tl;
-  }
   if (act && out != SEG_CONTINUE) {
-    if (want_tail && !(my_tail <= s.trunc_tol)) out = SEG_FAIL_TRUNC;
+    if ((out == SEG_OK || out == SEG_STALLED) && s.trunc_tol > 0.0 && !(tail_estimate(s, tails, m) <= s.trunc_tol))
+      out = SEG_FAIL_TRUNC;
     const int D = s.max_depth;
     bool accept = (out == SEG_OK || out == SEG_STALLED);
     if (out == SEG_FAIL_TRUNC && c.depth[m] >= D) {
@@ -1022,8 +1094,10 @@ constexpr size_t kFp32KsmemLimit = 120 * 1024;
 
 template <int NPL>
 void launch_fp32(const pc_plan *p, const Sweep &s, double *Y, const Mix &mx, cudaStream_t st) {
-  const size_t k_bytes = (size_t)p->n * 32 * NPL * sizeof(float);
-  const size_t g_bytes = (size_t)kFp32Warps * p->n * 6 * sizeof(float);
+  const int n4 = (p->n + 3) & ~3;
+  const int lstride = ((NPL * n4 + 31) & ~31) + 4;
+  const size_t k_bytes = (size_t)32 * lstride * sizeof(float);
+  const size_t g_bytes = (size_t)kFp32Warps * n4 * 6 * sizeof(float);
   const Ctl &c = p->ws.ctl[p->ws.live];
   if (k_bytes + g_bytes <= kFp32KsmemLimit) {
     cudaFuncSetAttribute(k_fp32<NPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k_bytes + g_bytes));
@@ -1072,14 +1146,16 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
     }
   }
   if (ev) cudaEventRecord(ev[2], st);
-  k_force<<<dim3(blocks_for(s.A, kThreads), s.n), kThreads, 0, st>>>(s, c, p->model, Yc, E, Ai, w.G);
+  k_force<<<dim3(blocks_for(s.A, 32), (s.n + kForceNodes - 1) / kForceNodes), dim3(32, kForceNodes), 0, st>>>(
+      s, c, p->model, Yc, E, Ai, w.G, p->d_tau, w.tails);
   if (ev) cudaEventRecord(ev[3], st);
   // persistent FP64 contraction: 4 CTAs of kSplit warps per SM
   const long long tiles = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
   const long long blocks = std::min<long long>(152 * 4, tiles);
   k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn);
   if (ev) cudaEventRecord(ev[4], st);
-  k_control<<<blocks_for(s.A, kThreads), kThreads, 0, st>>>(s, c, p->d_tau, w.G, Yn, w.ints);
+  // one warp per block: the control work (resolution tests) spreads over all SMs
+  k_control<<<blocks_for(s.A, 32), 32, 0, st>>>(s, c, w.tails, Yn, w.ints);
   if (ev) cudaEventRecord(ev[5], st);
   p->acc_launches += s.mixed ? 5 : 4;
   return cudaGetLastError();
