@@ -54,6 +54,7 @@ typedef enum {
 #define PC_IC_UNRESOLVED 2     /* a segment at the deepest halving still failed the resolution test */
 #define PC_IC_NOT_CONVERGED 4  /* stopped: a segment did not converge even at the deepest halving */
 #define PC_IC_NONFINITE 8      /* stopped: non-finite input, or the iteration blew up at the deepest halving */
+#define PC_IC_OUT_OF_RANGE 16  /* refused: the arc leaves the ephemeris table, or a bad per-trajectory arc */
 
 /* Force model: a(r, t) = -mu_c r/|r|^3 - sum_b mu_b [(r - r_b)/|r - r_b|^3 + r_b/|r_b|^3]
  * (heliocentric Newtonian point masses; the bracket's second term, the
@@ -224,6 +225,28 @@ pc_status pc_plan_set_profiling(pc_plan *plan, int on);
  * events) and clears them.  The sweep and launch counts cover every call since
  * the previous pc_plan_kernel_times, whether profiling was on or not. */
 pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
+
+/* Uneven batching: n_groups groups of trajectories, group g propagated with
+ * plans[g] (its own degree N, segment count and options) -- the paper's
+ * two-level augmentation (Section "Two-level augmentation") with the outer
+ * level keyed by degree.  The trajectories are one batch in planar layout,
+ * group g at columns [counts[0] + .. + counts[g-1], + counts[g]) of
+ *   x0, xf      device, planar [6][n_total]
+ *   t0, tf      device [n_total]: each trajectory's own arc (tf < t0 backward)
+ *   segments    device [n_total] base segment count per trajectory, or NULL
+ *               (the plan's); per arc or per osculating period as the plan's
+ *               seg_mode says
+ *   status, iters, nseg   device [n_total] or NULL
+ * Each group runs its own rounds (with its own compaction of finished
+ * trajectories) on a stream of its plan, forked from and joined back to
+ * `stream`; the host steps the groups in turn, so all groups keep the GPU busy
+ * together.  A plan may appear once (its workspace serves one group).  An arc
+ * outside a plan's ephemeris table sets PC_IC_OUT_OF_RANGE for that trajectory.
+ * rounds: host, total sweep rounds over the groups, or NULL.
+ * Returns PC_OK, PC_ENOTCONV, PC_EINVAL, PC_ENOMEM or PC_ECUDA. */
+pc_status pc_propagate_groups(pc_plan *const *plans, int n_groups, const long long *counts, const double *x0,
+                              const double *t0, const double *tf, const int *segments, double tol, double *xf,
+                              int *status, int *iters, int *nseg, long long *rounds, void *stream);
 
 /* Copies the plan's operator K ((N+1) x (N+1), row-major) and nodes tau (N+1)
  * to host buffers (either may be NULL).  For tests and diagnostics. */

@@ -1,5 +1,6 @@
 // Host driver of the batched sweep and the kernel-level entry points.
 #include <cmath>
+#include <vector>
 
 #include "pc_internal.h"
 
@@ -19,36 +20,52 @@ constexpr int kRoundsPerBatch = 8;
 
 }  // namespace
 
-extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x0, double t0, double tf,
-                                     double tol, double *xf, int *status, int *iters, int *nseg, int max_ckpt,
-                                     double *ckpt, long long *rounds_out, void *stream) {
-  if (rounds_out) *rounds_out = 0;
-  if (!p || n_ic < 0) return PC_EINVAL;
-  if (n_ic == 0) return PC_OK;
-  if (!x0 || !xf || !std::isfinite(t0) || !std::isfinite(tf) || max_ckpt < 0 || (max_ckpt > 0 && !ckpt))
-    return PC_EINVAL;
-  if (n_ic > (1LL << 30)) return PC_EINVAL;
-  const Model &md = p->model;
-  if (md.B > 0) {
-    const double lo = md.t_begin, hi = md.t_begin + md.granule * md.n_gr;
-    if (std::fmin(t0, tf) < lo || std::fmax(t0, tf) > hi) return PC_EINVAL;
-  }
+namespace {
+
+// One propagation in flight on one plan: the host side of the round loop.
+// begin() sets the call up and launches the initialisation, step() queues a
+// batch of rounds and looks at the previous batch's counters (repacking the
+// working set when 1/8 of it has finished), finish() closes the call.  The
+// multi-group entry point steps several sessions in turn on their own streams.
+struct Session {
+  pc_plan *p = nullptr;
+  Sweep s{};
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaSuccess;
+  long long n_ic = 0, rounds = 0, max_rounds = 0;
+  int cur = 0, pending = -1, done_known = 0;
+  bool finished = false, capped = false;
+};
+
+struct Arcs {
+  double t0s, tfs;          // scalar arc (when the arrays are NULL)
+  const double *t0a, *tfa;  // device, per trajectory, or NULL
+  const int *sega;          // device, per trajectory, or NULL
+};
+
+pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld, long long io_off, const double *x0,
+                        const Arcs &arcs, double tol, double *xf, int *status, int *iters, int *nseg, int max_ckpt,
+                        double *ckpt, cudaStream_t st) {
   const pc_options &o = p->opt;
   const int mixed = o.precision == PC_PREC_MIXED ? 1 : 0;
   pc_status ps = ensure_workspace(p, n_ic, mixed);
   if (ps != PC_OK) return ps;
-  cudaStream_t st = (cudaStream_t)stream;
-  Sweep s{};
+  Workspace &w = p->ws;
+  Sweep &s = S.s;
+  s = Sweep{};
   s.N = p->N;
   s.n = p->n;
   s.kpad = p->kpad;
   s.rows_pad = p->rows_pad;
   s.n_ic = n_ic;
-  s.ld = p->ws.ld;
-  s.t0 = t0;
-  s.tf = tf;
-  s.total = std::fabs(tf - t0);
-  s.sgn = (tf >= t0) ? 1.0 : -1.0;
+  s.ld = w.ld;
+  s.t0s = arcs.t0s;
+  s.tfs = arcs.tfs;
+  s.t0a = arcs.t0a;
+  s.tfa = arcs.tfa;
+  s.sega = arcs.sega;
+  s.io_ld = io_ld;
+  s.io_off = io_off;
   s.segments = p->segments;
   s.seg_mode = o.seg_mode;
   s.max_depth = o.max_depth;
@@ -62,7 +79,6 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
   s.trunc_tol = o.trunc_tol;
   s.max_ckpt = max_ckpt;
   s.ckpt = max_ckpt > 0 ? ckpt : nullptr;
-  Workspace &w = p->ws;
   s.xf = xf;
   s.status = status;
   s.iters = iters;
@@ -80,83 +96,187 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
   s.list_cur = 0;
   s.A = (int)n_ic;
   w.live = 0;
+  S.p = p;
+  S.st = st;
+  S.n_ic = n_ic;
+  S.rounds = 0;
+  S.max_rounds = o.max_rounds > 0 ? o.max_rounds : 10000000LL;
+  S.cur = 0;
+  S.pending = -1;
+  S.done_known = 0;
+  S.finished = S.capped = false;
+  S.e = launch_init(p, s, x0, st);
+  return S.e == cudaSuccess ? PC_OK : cuda_status(S.e);
+}
 
-  cudaError_t e = launch_init(p, s, x0, st);
-  const long long max_rounds = o.max_rounds > 0 ? o.max_rounds : 10000000LL;
-  long long rounds = 0;
-  int cur = 0;
-  int pending = -1;         // slot of the batch whose counter copy is in flight
-  int done_known = 0;       // finished trajectories at the last completed check
-  bool finished = false, capped = false;
-  while (e == cudaSuccess && !finished) {
-    for (int r = 0; r < kRoundsPerBatch && e == cudaSuccess && s.A > 0; r++) {
-      cudaEvent_t *ev = nullptr;
-      if (p->prof_on) {
-        const size_t need = (size_t)(p->prof_rounds + 1) * 6;
-        while (e == cudaSuccess && p->prof_ev.size() < need) {
-          cudaEvent_t x;
-          e = cudaEventCreate(&x);
-          if (e == cudaSuccess) p->prof_ev.push_back(x);
-        }
-        if (e != cudaSuccess) break;
-        ev = p->prof_ev.data() + (size_t)p->prof_rounds * 6;
-        p->prof_rounds++;
+void session_step(Session &S) {
+  if (S.finished || S.e != cudaSuccess) return;
+  pc_plan *p = S.p;
+  Sweep &s = S.s;
+  Workspace &w = p->ws;
+  cudaError_t &e = S.e;
+  for (int r = 0; r < kRoundsPerBatch && e == cudaSuccess && s.A > 0; r++) {
+    cudaEvent_t *ev = nullptr;
+    if (p->prof_on) {
+      const size_t need = (size_t)(p->prof_rounds + 1) * 6;
+      while (e == cudaSuccess && p->prof_ev.size() < need) {
+        cudaEvent_t x;
+        e = cudaEventCreate(&x);
+        if (e == cudaSuccess) p->prof_ev.push_back(x);
       }
-      e = launch_round(p, s, cur, st, ev);
-      cur ^= 1;
-      s.list_cur ^= 1;
-      rounds++;
+      if (e != cudaSuccess) return;
+      ev = p->prof_ev.data() + (size_t)p->prof_rounds * 6;
+      p->prof_rounds++;
     }
-    if (e != cudaSuccess) break;
-    const int slot = (pending < 0) ? 0 : (pending ^ 1);
-    e = cudaMemcpyAsync(w.h_ints + 8 * slot, w.ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaEventRecord(w.ev[slot], st);
-    if (e != cudaSuccess) break;
-    if (pending >= 0) {
-      e = cudaEventSynchronize(w.ev[pending]);
-      if (e != cudaSuccess) break;
-      done_known = w.h_ints[8 * pending];
-      if (done_known >= n_ic) finished = true;
-    }
-    pending = slot;
-    if (finished) break;
-    if (rounds >= max_rounds) {
-      capped = true;
-      break;
-    }
-    // Compaction: when at least 1/8 of the slots hold finished trajectories,
-    // move the active ones to the front so later rounds launch over fewer slots.
-    const long long active = n_ic - done_known;
-    const long long dead = (long long)s.A - active;
-    if (dead > 0 && dead * 8 >= (long long)s.A) {
-      e = launch_repack(p, s, cur, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints + 16, w.ints + 4, sizeof(int), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) break;
-      s.A = w.h_ints[16];
-      cur ^= 1;
-      w.live ^= 1;
-      pending = -1;
-      if (s.A == 0) finished = true;
-    }
+    e = launch_round(p, s, S.cur, S.st, ev);
+    S.cur ^= 1;
+    s.list_cur ^= 1;
+    S.rounds++;
   }
-  if (e == cudaSuccess && capped) e = launch_abort(p, s, st);
+  if (e != cudaSuccess) return;
+  const int slot = (S.pending < 0) ? 0 : (S.pending ^ 1);
+  e = cudaMemcpyAsync(w.h_ints + 8 * slot, w.ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, S.st);
+  if (e == cudaSuccess) e = cudaEventRecord(w.ev[slot], S.st);
+  if (e != cudaSuccess) return;
+  if (S.pending >= 0) {
+    e = cudaEventSynchronize(w.ev[S.pending]);
+    if (e != cudaSuccess) return;
+    S.done_known = w.h_ints[8 * S.pending];
+    if (S.done_known >= S.n_ic) S.finished = true;
+  }
+  S.pending = slot;
+  if (S.finished) return;
+  if (S.rounds >= S.max_rounds) {
+    S.capped = true;
+    S.finished = true;
+    return;
+  }
+  // Compaction: when at least 1/8 of the slots hold finished trajectories,
+  // move the active ones to the front so later rounds launch over fewer slots.
+  const long long active = S.n_ic - S.done_known;
+  const long long dead = (long long)s.A - active;
+  if (dead > 0 && dead * 8 >= (long long)s.A) {
+    e = launch_repack(p, s, S.cur, S.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints + 16, w.ints + 4, sizeof(int), cudaMemcpyDeviceToHost, S.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
+    if (e != cudaSuccess) return;
+    s.A = w.h_ints[16];
+    S.cur ^= 1;
+    w.live ^= 1;
+    S.pending = -1;
+    if (s.A == 0) S.finished = true;
+  }
+}
+
+pc_status session_finish(Session &S, long long *rounds_out) {
+  pc_plan *p = S.p;
+  Workspace &w = p->ws;
+  cudaError_t e = S.e;
+  if (e == cudaSuccess && S.capped) e = launch_abort(p, S.s, S.st);
   // aggregate: did any trajectory stop early?
-  if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints, w.ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints, w.ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, S.st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(w.h_cnt64, w.cnt64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (rounds_out) *rounds_out = rounds;
+    e = cudaMemcpyAsync(w.h_cnt64, w.cnt64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, S.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
+  if (rounds_out) *rounds_out += S.rounds;
   if (e != cudaSuccess) return cuda_status(e);
   p->acc_sweeps64 += (long long)w.h_cnt64[0];
   p->acc_sweeps32 += (long long)w.h_cnt64[1];
-  if (capped || w.h_ints[1] > 0) return PC_ENOTCONV;
+  if (S.capped || w.h_ints[1] > 0) return PC_ENOTCONV;
   return PC_OK;
+}
+
+}  // namespace
+
+extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x0, double t0, double tf,
+                                     double tol, double *xf, int *status, int *iters, int *nseg, int max_ckpt,
+                                     double *ckpt, long long *rounds_out, void *stream) {
+  if (rounds_out) *rounds_out = 0;
+  if (!p || n_ic < 0) return PC_EINVAL;
+  if (n_ic == 0) return PC_OK;
+  if (!x0 || !xf || !std::isfinite(t0) || !std::isfinite(tf) || max_ckpt < 0 || (max_ckpt > 0 && !ckpt))
+    return PC_EINVAL;
+  if (n_ic > (1LL << 30)) return PC_EINVAL;
+  const Model &md = p->model;
+  if (md.B > 0) {
+    const double lo = md.t_begin, hi = md.t_begin + md.granule * md.n_gr;
+    if (std::fmin(t0, tf) < lo || std::fmax(t0, tf) > hi) return PC_EINVAL;
+  }
+  Session S;
+  const Arcs arcs{t0, tf, nullptr, nullptr, nullptr};
+  pc_status ps = session_begin(S, p, n_ic, n_ic, 0, x0, arcs, tol, xf, status, iters, nseg, max_ckpt, ckpt,
+                               (cudaStream_t)stream);
+  if (ps != PC_OK) return ps;
+  while (!S.finished && S.e == cudaSuccess) session_step(S);
+  return session_finish(S, rounds_out);
 }
 
 extern "C" pc_status pc_propagate(pc_plan *p, long long n_ic, const double *x0, double t0, double tf, double tol,
                                   double *xf, int *status, int *iters, void *stream) {
   return pc_propagate_ex(p, n_ic, x0, t0, tf, tol, xf, status, iters, nullptr, 0, nullptr, nullptr, stream);
+}
+
+extern "C" pc_status pc_propagate_groups(pc_plan *const *plans, int n_groups, const long long *counts,
+                                         const double *x0, const double *t0, const double *tf, const int *segments,
+                                         double tol, double *xf, int *status, int *iters, int *nseg,
+                                         long long *rounds_out, void *stream) {
+  if (rounds_out) *rounds_out = 0;
+  if (!plans || n_groups < 1 || n_groups > 64 || !counts || !t0 || !tf) return PC_EINVAL;
+  long long total = 0;
+  for (int g = 0; g < n_groups; g++) {
+    if (!plans[g] || counts[g] < 0) return PC_EINVAL;
+    for (int h = 0; h < g; h++)
+      if (plans[h] == plans[g] && counts[g] > 0 && counts[h] > 0) return PC_EINVAL;  // one workspace per group
+    total += counts[g];
+  }
+  if (total == 0) return PC_OK;
+  if (!x0 || !xf || total > (1LL << 30)) return PC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // fork: every group waits for the caller's stream, runs on its plan's own
+  // stream, and the caller's stream waits for all groups at the end
+  cudaEvent_t fork = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+  std::vector<Session> S(n_groups);
+  pc_status result = PC_OK;
+  long long off = 0;
+  for (int g = 0; g < n_groups && e == cudaSuccess; g++) {
+    pc_plan *p = plans[g];
+    if (counts[g] > 0) {
+      if (!p->own_stream) e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->own_stream, fork, 0);
+      if (e != cudaSuccess) break;
+      const Arcs arcs{0.0, 0.0, t0, tf, segments};
+      pc_status ps = session_begin(S[g], p, counts[g], total, off, x0, arcs, tol, xf, status, iters, nseg, 0,
+                                   nullptr, p->own_stream);
+      if (ps != PC_OK) {
+        result = ps;
+        S[g].finished = true;
+      }
+    } else {
+      S[g].finished = true;
+    }
+    off += counts[g];
+  }
+  bool busy = true;
+  while (busy && e == cudaSuccess) {
+    busy = false;
+    for (int g = 0; g < n_groups; g++) {
+      if (S[g].finished || S[g].e != cudaSuccess) continue;
+      session_step(S[g]);
+      busy = busy || (!S[g].finished && S[g].e == cudaSuccess);
+    }
+  }
+  for (int g = 0; g < n_groups; g++) {
+    if (counts[g] == 0 || !S[g].p) continue;
+    pc_status ps = session_finish(S[g], rounds_out);
+    if (ps != PC_OK && result == PC_OK) result = ps;
+    if (e == cudaSuccess) e = cudaEventRecord(fork, plans[g]->own_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fork, 0);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (e != cudaSuccess) return cuda_status(e);
+  return result;
 }
 
 extern "C" pc_status pc_eval_ephemeris(pc_plan *p, long long n, const double *t, double *rb, void *stream) {

@@ -40,6 +40,8 @@ struct Model {
 // trajectory's index in the caller's arrays.
 struct Ctl {
   double *x;          // [6][ld] state at the start of the current segment
+  double *t0, *tf;    // the trajectory's arc
+  double *total, *sgn;  // |tf - t0| and sign(tf - t0)
   double *hbase;      // base segment length
   double *ta, *tb, *w1, *w2;
   double *e_best;
@@ -48,7 +50,7 @@ struct Ctl {
   int *depth, *phase, *status, *sweeps, *seg_sweeps, *nstall, *nseg, *need_setup, *last, *ic;
   unsigned *err32;    // final FP32-phase change of a trajectory whose FP32 phase blew up
 };
-constexpr int kCtlDoubles = 12;  // x[6] + hbase, ta, tb, w1, w2, e_best
+constexpr int kCtlDoubles = 16;  // x[6] + t0, tf, total, sgn, hbase, ta, tb, w1, w2, e_best
 constexpr int kCtlInts = 11;     // 10 ints + err32
 
 // Sweep parameters of one call.
@@ -57,7 +59,13 @@ struct Sweep {
   long long n_ic;
   int ld;                    // leading dimension over slots (multiple of 8)
   int A;                     // slots [0, A) may hold active trajectories
-  double t0, tf, total, sgn;
+  // arcs: per trajectory from t0a / tfa / sega when given, else t0s / tfs / segments
+  double t0s, tfs;
+  const double *t0a, *tfa;
+  const int *sega;
+  // caller arrays hold this call's trajectories at columns io_off .. io_off + n_ic - 1
+  // of planar arrays with leading dimension io_ld
+  long long io_ld, io_off;
   int segments, seg_mode, max_depth, max_iters, stall_sweeps, relative, warm;
   double tol, stall_factor, div_limit, trunc_tol;
   int mixed;                 // 1: segments start with FP32 sweeps
@@ -124,6 +132,7 @@ struct pc_plan {
   pcx::Workspace ws;
   // per-kernel timing: 6 events per recorded round (before setup, force,
   // contract, the FP32 kernels, control, after control)
+  cudaStream_t own_stream = nullptr;  // created for multi-group calls
   int prof_on = 0;
   std::vector<cudaEvent_t> prof_ev;
   long long prof_rounds = 0;

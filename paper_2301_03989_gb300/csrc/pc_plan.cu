@@ -193,6 +193,10 @@ void carve_ctl(void *block, long long ld, Ctl &t) {
   char *c = (char *)block;
   auto take = [&](size_t each) { char *r = c; c += each * ld; return r; };
   t.x = (double *)take(8 * 6);
+  t.t0 = (double *)take(8);
+  t.tf = (double *)take(8);
+  t.total = (double *)take(8);
+  t.sgn = (double *)take(8);
   t.hbase = (double *)take(8);
   t.ta = (double *)take(8);
   t.tb = (double *)take(8);
@@ -286,6 +290,7 @@ extern "C" void pc_plan_destroy(pc_plan *p) {
   if (!p) return;
   free_workspace(p);
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+  if (p->own_stream) cudaStreamDestroy(p->own_stream);
   cudaFree(p->d_K);
   cudaFree(p->d_K32T);
   cudaFree(p->d_tau);

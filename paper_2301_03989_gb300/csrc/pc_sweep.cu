@@ -71,14 +71,15 @@ __device__ void schedule(const Sweep &s, Ctl &c, int m, int list_next) {
   const double u = scalbn(c.hbase[m], -D);
   const long long L = 1LL << (D - c.depth[m]);
   const long long p = c.p[m];
-  const double ta = dadd(s.t0, dmul(s.sgn, dmul((double)p, u)));
+  const double t0 = c.t0[m], sgn = c.sgn[m];
+  const double ta = dadd(t0, dmul(sgn, dmul((double)p, u)));
   double tb;
   int last = 0;
-  if (dmul((double)(p + L), u) >= s.total) {
-    tb = s.tf;
+  if (dmul((double)(p + L), u) >= c.total[m]) {
+    tb = c.tf[m];
     last = 1;
   } else {
-    tb = dadd(s.t0, dmul(s.sgn, dmul((double)(p + L), u)));
+    tb = dadd(t0, dmul(sgn, dmul((double)(p + L), u)));
   }
   c.ta[m] = ta;
   c.tb[m] = tb;
@@ -96,8 +97,8 @@ __device__ void schedule(const Sweep &s, Ctl &c, int m, int list_next) {
 
 // Final outputs of a trajectory, written when it finishes.
 __device__ __forceinline__ void write_outputs(const Sweep &s, const Ctl &c, int m) {
-  const long long i = c.ic[m];
-  for (int q = 0; q < 6; q++) s.xf[q * s.n_ic + i] = c.x[q * s.ld + m];
+  const long long i = s.io_off + c.ic[m];
+  for (int q = 0; q < 6; q++) s.xf[q * s.io_ld + i] = c.x[q * s.ld + m];
   if (s.status) s.status[i] = c.status[m];
   if (s.iters) s.iters[i] = c.sweeps[m];
   if (s.nseg) s.nseg[i] = c.nseg[m];
@@ -112,11 +113,25 @@ __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, 
     double x[6];
     bool finite = true;
     for (int q = 0; q < 6; q++) {
-      x[q] = x0[q * s.n_ic + m];
+      x[q] = x0[q * s.io_ld + s.io_off + m];
       c.x[q * ld + m] = x[q];
       finite = finite && isfinite(x[q]);
     }
-    double h = s.total / (double)s.segments;
+    const double t0 = s.t0a ? s.t0a[s.io_off + m] : s.t0s;
+    const double tf = s.tfa ? s.tfa[s.io_off + m] : s.tfs;
+    const int segs = s.sega ? s.sega[s.io_off + m] : s.segments;
+    const double total = fabs(dsub(tf, t0));
+    c.t0[m] = t0;
+    c.tf[m] = tf;
+    c.total[m] = total;
+    c.sgn[m] = (tf >= t0) ? 1.0 : -1.0;
+    // an arc outside the ephemeris table, or a bad segment count, is refused
+    bool arc_ok = isfinite(t0) && isfinite(tf) && segs >= 1;
+    if (md.B > 0) {
+      const double lo = md.t_begin, hi = dadd(md.t_begin, dmul(md.granule, (double)md.n_gr));
+      arc_ok = arc_ok && fmin(t0, tf) >= lo && fmax(t0, tf) <= hi;
+    }
+    double h = total / (double)(segs >= 1 ? segs : 1);
     if (s.seg_mode == 1 && finite) {
       const double r0 = sqrt(dadd(dadd(dmul(x[0], x[0]), dmul(x[1], x[1])), dmul(x[2], x[2])));
       const double v2 = dadd(dadd(dmul(x[3], x[3]), dmul(x[4], x[4])), dmul(x[5], x[5]));
@@ -124,24 +139,24 @@ __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, 
       if (alpha > 0.0) {
         const double a = 1.0 / alpha;
         const double twopi = 6.283185307179586;  // 2 * M_PI rounded
-        h = dmul(twopi, sqrt(dmul(dmul(a, a), a) / md.mu_c)) / (double)s.segments;
+        h = dmul(twopi, sqrt(dmul(dmul(a, a), a) / md.mu_c)) / (double)(segs >= 1 ? segs : 1);
       }
     }
     c.ic[m] = m;
     c.hbase[m] = h;
     c.p[m] = 0;
     c.depth[m] = 0;
-    c.status[m] = finite ? 0 : PC_IC_NONFINITE;
+    c.status[m] = (finite ? 0 : PC_IC_NONFINITE) | (arc_ok ? 0 : PC_IC_OUT_OF_RANGE);
     c.sweeps[m] = 0;
     c.nseg[m] = 0;
     c.err[m] = 0ULL;
     c.err32[m] = 0u;
     c.need_setup[m] = 0;
-    if (!finite || !(s.total > 0.0)) {
+    if (!finite || !arc_ok || !(total > 0.0)) {
       c.phase[m] = PH_DONE;
       write_outputs(s, c, m);
       atomicAdd(done, 1);
-      if (!finite) atomicAdd(done + 1, 1);
+      if (!finite || !arc_ok) atomicAdd(done + 1, 1);
     } else {
       schedule(s, c, m, s.list_cur);
       to64 = c.phase[m] == PH_ITER;
@@ -927,7 +942,7 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
       if (out == SEG_STALLED) c.status[m] |= PC_IC_STALLED;
       const int k = c.nseg[m];
       if (s.ckpt && k < s.max_ckpt) {
-        double *ck = s.ckpt + ((size_t)c.ic[m] * s.max_ckpt + k) * 7;
+        double *ck = s.ckpt + ((size_t)(s.io_off + c.ic[m]) * s.max_ckpt + k) * 7;
         ck[0] = c.ta[m];
         for (int q = 0; q < 6; q++) ck[1 + q] = c.x[q * ld + m];
       }
@@ -997,6 +1012,10 @@ __global__ void k_repack_ctl(Sweep s, Ctl a, Ctl b, const int *__restrict__ pos)
   if (d >= 0) {
     const int ld = s.ld;
     for (int q = 0; q < 6; q++) b.x[q * ld + d] = a.x[q * ld + m];
+    b.t0[d] = a.t0[m];
+    b.tf[d] = a.tf[m];
+    b.total[d] = a.total[m];
+    b.sgn[d] = a.sgn[m];
     b.hbase[d] = a.hbase[m];
     b.ta[d] = a.ta[m];
     b.tb[d] = a.tb[m];

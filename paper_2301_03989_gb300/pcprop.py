@@ -19,12 +19,13 @@ _lock = threading.Lock()
 _lib = None
 
 PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOTCONV, PC_ENONFINITE = 0, 1, 2, 3, 4, 5
-PC_IC_STALLED, PC_IC_UNRESOLVED, PC_IC_NOT_CONVERGED, PC_IC_NONFINITE = 1, 2, 4, 8
+PC_IC_STALLED, PC_IC_UNRESOLVED, PC_IC_NOT_CONVERGED, PC_IC_NONFINITE, PC_IC_OUT_OF_RANGE = 1, 2, 4, 8, 16
 PC_PREC_FP64, PC_PREC_MIXED = 0, 1
 
 EXPORTS = ["pc_options_default", "pc_plan_create", "pc_propagate", "pc_propagate_ex", "pc_eval_ephemeris",
            "pc_eval_dynamics", "pc_eval_warm_start", "pc_apply_operator", "pc_plan_operator", "pc_plan_destroy",
-           "pc_status_string", "pc_plan_set_profiling", "pc_plan_kernel_times", "pc_apply_operator_static"]
+           "pc_status_string", "pc_plan_set_profiling", "pc_plan_kernel_times", "pc_apply_operator_static",
+           "pc_propagate_groups"]
 KERNEL_NAMES = ["setup", "fp32", "force", "contract", "control"]
 
 
@@ -75,6 +76,8 @@ def lib():
             L.pc_eval_warm_start.argtypes = [vp, ll, vp, vp, vp, vp]
             L.pc_apply_operator.argtypes = [vp, ll, vp, vp, vp, vp]
             L.pc_apply_operator_static.argtypes = [vp, ll, vp, vp, vp, vp]
+            L.pc_propagate_groups.argtypes = [C.POINTER(vp), i, C.POINTER(ll), vp, vp, vp, vp, d, vp, vp, vp, vp,
+                                              C.POINTER(ll), vp]
             L.pc_plan_operator.argtypes = [vp, vp, vp]
             L.pc_plan_destroy.argtypes = [vp]
             L.pc_plan_destroy.restype = None
@@ -190,6 +193,21 @@ def propagate(plan: Plan, x0, t0: float, tf: float, xf, tol: float = 0.0, status
                                  _ptr(status), _ptr(iters), _ptr(nseg), int(max_ckpt), _ptr(ckpt),
                                  C.byref(rounds), _stream(stream))
     _check(code, "pc_propagate", ok=(PC_OK, PC_ENOTCONV))
+    return code, int(rounds.value)
+
+
+def propagate_groups(plans, counts, x0, t0, tf, xf, segments=None, tol: float = 0.0, status=None, iters=None,
+                     nseg=None, stream=None) -> tuple[int, int]:
+    """Uneven batch: group g (plans[g], counts[g] trajectories) occupies the
+    next counts[g] columns of x0/xf (planar [6][n_total]) and entries of t0, tf,
+    segments (int32), status, iters, nseg.  Returns (pc_status, total rounds)."""
+    n = len(plans)
+    hp = (C.c_void_p * n)(*[p.handle for p in plans])
+    hc = (C.c_longlong * n)(*[int(c) for c in counts])
+    rounds = C.c_longlong(0)
+    code = lib().pc_propagate_groups(hp, n, hc, _ptr(x0), _ptr(t0), _ptr(tf), _ptr(segments), float(tol), _ptr(xf),
+                                     _ptr(status), _ptr(iters), _ptr(nseg), C.byref(rounds), _stream(stream))
+    _check(code, "pc_propagate_groups", ok=(PC_OK, PC_ENOTCONV))
     return code, int(rounds.value)
 
 

@@ -280,6 +280,60 @@ def config3(M: int = 65536, seed: int = 3) -> Workload:
                     meta=dict(seed=seed))
 
 
+# --------------------------------------------------------------------------
+# Config 5: uneven batching -- per-trajectory durations, degrees and segments
+# --------------------------------------------------------------------------
+# Segments per revolution of the config-1 orbit at which the oracle converges to
+# 1e-13 within 40 sweeps without halving, by degree (oracle/calibrate_segment_lengths.py).
+SEGMENTS_PER_REV = {32: 4, 64: 2, 128: 1, 256: 1}
+
+
+@dataclass
+class UnevenWorkload:
+    """Per-trajectory arcs [t0, tf], degrees N and base segment counts S."""
+    name: str
+    base: Workload            # force model, tables, options (N, segments unused)
+    x0: np.ndarray            # [M][6]
+    t0: np.ndarray            # [M]
+    tf: np.ndarray            # [M]
+    N: np.ndarray             # [M] Chebyshev degree per trajectory
+    S: np.ndarray             # [M] base segments per trajectory (per arc)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_ic(self) -> int:
+        return int(self.x0.shape[0])
+
+    def groups(self):
+        """Stable order by degree: (perm, degrees, counts) -- perm lists the
+        trajectories group by group."""
+        degs = sorted(set(int(n) for n in self.N))
+        perm = np.concatenate([np.flatnonzero(self.N == d) for d in degs])
+        counts = [int((self.N == d).sum()) for d in degs]
+        return perm, degs, counts
+
+
+def config5(M: int = 1048576, seed: int = 5, years_max: float = 10.0) -> UnevenWorkload:
+    """Config-1 system and IC distribution; durations D ~ U(0.5, years_max) yr,
+    degree N ~ U{32, 64, 128, 256}, S = clamp(ceil(D / L(N)), 4, 80) with
+    L(N) = revolution / SEGMENTS_PER_REV[N]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    names, bodies = _circular_system()
+    a = 0.75 * AU
+    T = 2.0 * np.pi * np.sqrt(a**3 / MU_SUN)
+    tb, ng = _table_span(0.0, years_max * YEAR)
+    coef = fit_tables(bodies, tb, ng)
+    x0 = _jittered_ics(rng, M, a, 0.3, np.deg2rad(2.0))
+    D = rng.uniform(0.5, years_max, M) * YEAR
+    N = rng.choice(np.array([32, 64, 128, 256]), M)
+    L = np.array([T / SEGMENTS_PER_REV[int(n)] for n in N])
+    S = np.clip(np.ceil(D / L), 4, 80).astype(np.int32)
+    base = Workload(f"cfg5_sun_venus_earth_{M}ic_uneven", MU_SUN, names, np.array([GM[n] for n in names]),
+                    tb, GRANULE, coef, x0, 0.0, years_max * YEAR, N=128, segments=4, seg_mode=0, tol=1e-13,
+                    meta=dict(seed=seed))
+    return UnevenWorkload(base.name, base, x0, np.zeros(M), D, N.astype(np.int32), S, meta=dict(seed=seed))
+
+
 def to_planar(x: np.ndarray) -> np.ndarray:
     """[M][6] -> component-planar [6][M] (the paper's component-stacked layout)."""
     return np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 6).T)
