@@ -91,6 +91,16 @@ def lib():
             L.ora_gl_propagate.argtypes = [P(_Model), P(_Opts), C.c_int, P(C.c_double), C.c_double, C.c_double,
                                            C.c_long, P(C.c_double)]
             L.ora_gl_propagate.restype = C.c_int
+            L.ora_ephem_vel.argtypes = [P(_Model), C.c_double, P(C.c_double)]
+            L.ora_tidal.argtypes = [P(_Model), P(C.c_double), P(C.c_double), P(C.c_double)]
+            L.ora_stm_propagate.argtypes = [P(_Model), P(_Opts), P(C.c_double), C.c_int, P(C.c_double),
+                                            P(C.c_double), P(C.c_double), P(C.c_int)]
+            L.ora_stm_propagate.restype = C.c_int
+            L.ora_gl_stm_propagate.argtypes = [P(_Model), C.c_int, P(C.c_double), C.c_double, C.c_double,
+                                               C.c_long, P(C.c_double), P(C.c_double)]
+            L.ora_gl_stm_propagate.restype = C.c_int
+            L.ora_bplane.argtypes = [C.c_double, P(C.c_double), P(C.c_double)]
+            L.ora_bplane.restype = C.c_int
             _lib = L
     return _lib
 
@@ -259,3 +269,58 @@ def gl_propagate(model: Model, opts: Opts, x0, t0: float, tf: float, nsteps: int
     capped = lib().ora_gl_propagate(C.byref(s), C.byref(o), int(stages), _dp(x0), float(t0), float(tf),
                                     int(nsteps), _dp(xf))
     return xf, int(capped)
+
+
+# ---- differentiation checks ------------------------------------------------
+
+def ephem_vel(model: Model, t: float) -> np.ndarray:
+    """Body velocities [B][3] from the table (time derivative of the series)."""
+    s = model.struct()
+    out = np.zeros((max(s.n_bodies, 1), 3))
+    lib().ora_ephem_vel(C.byref(s), float(t), _dp(out))
+    return out[: s.n_bodies]
+
+
+def tidal(model: Model, rb: np.ndarray, r) -> np.ndarray:
+    """Gravity gradient da/dr [3][3] at r with body positions rb [B][3]."""
+    s = model.struct()
+    rb = np.ascontiguousarray(rb, dtype=np.float64).reshape(-1)
+    if rb.size == 0:
+        rb = np.zeros(3)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    A = np.zeros((3, 3))
+    lib().ora_tidal(C.byref(s), _dp(rb), _dp(r), _dp(A))
+    return A
+
+
+def stm_propagate(model: Model, opts: Opts, x0, bounds) -> tuple[np.ndarray, np.ndarray, int, int]:
+    """PC on the variational equations over the segment bounds [nseg+1].
+    Returns (xf [6], Phi [6][6] = d xf / d x0, segments that hit the cap, sweeps)."""
+    s, o = model.struct(), opts.struct()
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(6)
+    tb = np.ascontiguousarray(bounds, dtype=np.float64).reshape(-1)
+    xf = np.zeros(6)
+    Phi = np.zeros((6, 6))
+    sw = C.c_int(0)
+    capped = lib().ora_stm_propagate(C.byref(s), C.byref(o), _dp(x0), int(tb.size - 1), _dp(tb), _dp(xf), _dp(Phi),
+                                     C.byref(sw))
+    return xf, Phi, int(capped), int(sw.value)
+
+
+def gl_stm_propagate(model: Model, x0, t0: float, tf: float, nsteps: int, stages: int = 6):
+    """Gauss-Legendre collocation on the variational equations: (xf, Phi, capped steps)."""
+    s = model.struct()
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(6)
+    xf = np.zeros(6)
+    Phi = np.zeros((6, 6))
+    capped = lib().ora_gl_stm_propagate(C.byref(s), int(stages), _dp(x0), float(t0), float(tf), int(nsteps),
+                                        _dp(xf), _dp(Phi))
+    return xf, Phi, int(capped)
+
+
+def bplane(mu: float, rel) -> tuple[np.ndarray, int]:
+    """(B.T, B.R) of the planet-relative state rel = (r, v); rc 1 if not hyperbolic."""
+    rel = np.ascontiguousarray(rel, dtype=np.float64).reshape(6)
+    out = np.zeros(2)
+    rc = lib().ora_bplane(float(mu), _dp(rel), _dp(out))
+    return out, int(rc)

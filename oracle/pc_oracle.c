@@ -27,6 +27,14 @@
  *   ora_propagate        pinned: Gauss-Legendre collocation integrator,
  *                                forward/backward, batch invariance
  *   ora_gl_*             pinned: Legendre quadrature exactness, order check
+ *   ora_ephem_vel        pinned: numpy chebder/chebval, circular-orbit speed
+ *   ora_tidal            pinned: finite differences of ora_accel, zero trace
+ *   ora_stm_propagate    pinned: finite differences of analytic Kepler and of
+ *                                ora_propagate, symplecticity, Gauss-Legendre
+ *                                variational integration, composition
+ *   ora_gl_stm_propagate pinned: finite differences of ora_gl_propagate
+ *   ora_bplane           pinned: straight-line limit, hyperbola built from a
+ *                                chosen asymptote and aim point
  */
 #include <math.h>
 #include <pthread.h>
@@ -714,4 +722,293 @@ int ora_gl_propagate(const ora_model *m, const ora_opts *o, int s, const double 
   for (int q = 0; q < 6; q++) xf[q] = y[q];
   free(rb);
   return capped;
+}
+
+/* ================================================================== */
+/* Differentiation (reverse-mode checks).  None of this is in the paper */
+/* (its Conclusions name gradient-based trajectory optimisation as the  */
+/* use of a fast propagator); these routines give the derivatives the   */
+/* adjoint sweep of the CUDA library is checked against.                */
+/* ================================================================== */
+
+/* ------------------------------------------------------------------ */
+/* Body velocities from the ephemeris table: the time derivative of the */
+/* Chebyshev series of ora_ephem_eval,                                  */
+/*   dr_b/dt = (2/L) sum_{k>=1} c_k T_k'(sigma),  T_k' = k U_{k-1},     */
+/* U the Chebyshev polynomials of the second kind (U_0 = 1, U_1 = 2s,   */
+/* U_{k+1} = 2s U_k - U_{k-1}).  The b-plane needs the planet-relative  */
+/* velocity; the force itself needs positions only.  Same granule rule  */
+/* as ora_ephem_eval.  Degrees above 63 are not supported (zeros).      */
+/* ------------------------------------------------------------------ */
+void ora_ephem_vel(const ora_model *m, double t, double *vb /* [n_bodies][3] */) {
+  const int nc = m->degree + 1;
+  int g = (int)floor((t - m->t_begin) / m->granule);
+  if (g < 0) g = 0;
+  if (g > m->n_granules - 1) g = m->n_granules - 1;
+  const double tg = m->t_begin + (double)g * m->granule;
+  const double sigma = 2.0 * (t - tg) / m->granule - 1.0;
+  double U[64];
+  for (int b = 0; b < m->n_bodies; b++)
+    for (int ax = 0; ax < 3; ax++) vb[b * 3 + ax] = 0.0;
+  if (nc > 64) return;
+  U[0] = 1.0;
+  if (nc > 1) U[1] = 2.0 * sigma;
+  for (int k = 2; k < nc; k++) U[k] = 2.0 * sigma * U[k - 1] - U[k - 2];
+  for (int b = 0; b < m->n_bodies; b++) {
+    for (int ax = 0; ax < 3; ax++) {
+      const double *c = m->coef + (((size_t)b * m->n_granules + g) * 3 + ax) * nc;
+      double s = 0.0;
+      for (int k = 1; k < nc; k++) s += c[k] * (double)k * U[k - 1];
+      vb[b * 3 + ax] = s * 2.0 / m->granule;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Gravity gradient A = da/dr of ora_accel (row-major 3x3; the indirect */
+/* term does not depend on r):                                          */
+/*   A = -mu_S (I/|r|^3 - 3 r r^T/|r|^5)                                 */
+/*       - sum_b mu_b (I/|d|^3 - 3 d d^T/|d|^5),   d = r - r_b.          */
+/* ------------------------------------------------------------------ */
+static void ora_add_point_gradient(double mu, const double d[3], double A[9]) {
+  double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  double dn = sqrt(d2);
+  double i3 = 1.0 / (d2 * dn);
+  double i5 = i3 / d2;
+  for (int p = 0; p < 3; p++)
+    for (int q = 0; q < 3; q++) A[3 * p + q] -= mu * ((p == q ? i3 : 0.0) - 3.0 * d[p] * d[q] * i5);
+}
+
+void ora_tidal(const ora_model *m, const double *rb, const double r[3], double A[9]) {
+  for (int i = 0; i < 9; i++) A[i] = 0.0;
+  ora_add_point_gradient(m->mu_central, r, A);
+  for (int b = 0; b < m->n_bodies; b++) {
+    const double d[3] = {r[0] - rb[3 * b], r[1] - rb[3 * b + 1], r[2] - rb[3 * b + 2]};
+    ora_add_point_gradient(m->mu[b], d, A);
+  }
+}
+
+/* Variational equations of the N-body dynamics: z = (y, Phi), Phi the   */
+/* 6x6 state transition matrix (row-major), dPhi/dt = F(y) Phi with      */
+/* F = [[0, I], [A(r), 0]].                                               */
+static void ora_f_var(const ora_model *m, const double *rb, const double z[42], double fz[42]) {
+  fz[0] = z[3];
+  fz[1] = z[4];
+  fz[2] = z[5];
+  ora_accel(m, rb, z, fz + 3);
+  double A[9];
+  ora_tidal(m, rb, z, A);
+  const double *P = z + 6;
+  double *dP = fz + 6;
+  for (int col = 0; col < 6; col++) {
+    for (int q = 0; q < 3; q++) dP[q * 6 + col] = P[(3 + q) * 6 + col];
+    for (int q = 0; q < 3; q++) {
+      double s = 0.0;
+      for (int p = 0; p < 3; p++) s += A[3 * q + p] * P[p * 6 + col];
+      dP[(3 + q) * 6 + col] = s;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* The PC iteration of Eq. 2 on the variational equations, over a given */
+/* segment schedule tb[0] < tb[1] < ... < tb[nseg] (or decreasing), with */
+/* no halving: on segment k the 42 components z = (y, Phi) start from    */
+/* (x_k, Phi_k) and every sweep is z_j = z_0 + omega2 sum_k K_jk f(z_k).  */
+/* Node times, operator and the Kepler warm start of y are those of      */
+/* ora_pc_segment_core; Phi starts as Phi_k at every node.  A segment    */
+/* stops when the state change (the measure of ora_pc_segment_core) is  */
+/* below tol and the STM change max_j |dPhi_j|_F / |Phi_j|_F is too; or  */
+/* when the larger of the two has not improved for stall_sweeps sweeps   */
+/* while its best is below stall_factor*tol; or at max_iters.  Since the */
+/* y part is the state iteration and the Phi part is its linearisation   */
+/* at the same nodes, Phi is the derivative of the converged discrete    */
+/* map x0 -> xf.  Returns the number of segments that hit max_iters.    */
+/* ------------------------------------------------------------------ */
+int ora_stm_propagate(const ora_model *m, const ora_opts *o, const double x0[6], int nseg, const double *tb,
+                      double xf[6], double Phi[36], int *sweeps_out) {
+  const int N = o->N, n = N + 1, B = m->n_bodies;
+  double *K = (double *)malloc(sizeof(double) * n * n);
+  double *tau = (double *)malloc(sizeof(double) * n);
+  double *Z = (double *)malloc(sizeof(double) * 42 * n);
+  double *Zn = (double *)malloc(sizeof(double) * 42 * n);
+  double *G = (double *)malloc(sizeof(double) * 42 * n);
+  double *eph = (double *)malloc(sizeof(double) * (size_t)n * (B > 0 ? B : 1) * 3);
+  ora_pc_operator(N, o->truncated, K);
+  ora_cgl_nodes(N, tau);
+  double z0[42];
+  for (int c = 0; c < 6; c++) z0[c] = x0[c];
+  for (int i = 0; i < 36; i++) z0[6 + i] = (i % 7 == 0) ? 1.0 : 0.0;
+  int capped = 0, sweeps = 0;
+  for (int k = 0; k < nseg; k++) {
+    const double ta = tb[k], tbb = tb[k + 1];
+    const double w1 = 0.5 * (tbb + ta), w2 = 0.5 * (tbb - ta);
+    for (int j = 0; j < n; j++) {
+      const double t = w1 + w2 * tau[j];
+      if (B > 0) ora_ephem_eval(m, t, eph + (size_t)j * B * 3);
+      double *z = Z + 42 * j;
+      for (int c = 0; c < 42; c++) z[c] = z0[c];
+      if (j > 0 && o->warm_start) {
+        double y[6];
+        if (ora_kepler(m->mu_central, z0, t - ta, y) == 0)
+          for (int c = 0; c < 6; c++) z[c] = y[c];
+      }
+    }
+    double best = INFINITY;
+    int nstall = 0, done = 0, it;
+    for (it = 1; it <= o->max_iters && !done; it++) {
+      for (int j = 0; j < n; j++) ora_f_var(m, B ? eph + (size_t)j * B * 3 : NULL, Z + 42 * j, G + 42 * j);
+      for (int j = 0; j < n; j++)
+        for (int c = 0; c < 42; c++) {
+          double s = 0.0;
+          for (int q = 0; q < n; q++) s += K[j * n + q] * G[42 * q + c];
+          Zn[42 * j + c] = z0[c] + w2 * s;
+        }
+      double ey = 0.0, ep = 0.0;
+      for (int j = 0; j < n; j++) {
+        const double *a = Zn + 42 * j, *b = Z + 42 * j;
+        double dr = 0.0, dv = 0.0, nr = 0.0, nv = 0.0, dp = 0.0, np = 0.0;
+        for (int c = 0; c < 3; c++) {
+          dr += (a[c] - b[c]) * (a[c] - b[c]);
+          nr += a[c] * a[c];
+          dv += (a[3 + c] - b[3 + c]) * (a[3 + c] - b[3 + c]);
+          nv += a[3 + c] * a[3 + c];
+        }
+        for (int c = 6; c < 42; c++) {
+          dp += (a[c] - b[c]) * (a[c] - b[c]);
+          np += a[c] * a[c];
+        }
+        dr = sqrt(dr); dv = sqrt(dv); dp = sqrt(dp);
+        if (o->relative) {
+          if (nr > 0.0) dr /= sqrt(nr);
+          if (nv > 0.0) dv /= sqrt(nv);
+        }
+        if (np > 0.0) dp /= sqrt(np);
+        double e = dr > dv ? dr : dv;
+        if (!(e <= ey)) ey = e;
+        if (!(dp <= ep)) ep = dp;
+      }
+      memcpy(Z, Zn, sizeof(double) * 42 * n);
+      double e = ey > ep ? ey : ep;
+      if (ey < o->tol && ep < o->tol) {
+        done = 1;
+      } else {
+        if (e < best) { best = e; nstall = 0; } else { nstall++; }
+        if (nstall >= o->stall_sweeps && best < o->stall_factor * o->tol) done = 1;
+      }
+    }
+    sweeps += it - 1;
+    if (!done) capped++;
+    for (int c = 0; c < 42; c++) z0[c] = Z[42 * (n - 1) + c];
+  }
+  for (int c = 0; c < 6; c++) xf[c] = z0[c];
+  for (int i = 0; i < 36; i++) Phi[i] = z0[6 + i];
+  if (sweeps_out) *sweeps_out = sweeps;
+  free(K); free(tau); free(Z); free(Zn); free(G); free(eph);
+  return capped;
+}
+
+/* Gauss-Legendre collocation (the integrator of ora_gl_propagate) on the */
+/* variational equations: an independent check of ora_stm_propagate.      */
+int ora_gl_stm_propagate(const ora_model *m, int s, const double x0[6], double t0, double tf, long nsteps,
+                         double xf[6], double Phi[36]) {
+  double c[16], A[256], b[16];
+  ora_gl_coeffs(s, c, A, b);
+  const int B = m->n_bodies;
+  double *rb = (double *)malloc(sizeof(double) * 3 * (B > 0 ? B : 1));
+  double (*Kst)[42] = malloc(sizeof(double) * 16 * 42);
+  double (*Kn)[42] = malloc(sizeof(double) * 16 * 42);
+  double y[42], ys[42];
+  for (int q = 0; q < 6; q++) y[q] = x0[q];
+  for (int i = 0; i < 36; i++) y[6 + i] = (i % 7 == 0) ? 1.0 : 0.0;
+  const double h = (tf - t0) / (double)nsteps;
+  int capped = 0;
+  for (long st = 0; st < nsteps; st++) {
+    const double tn = t0 + (double)st * h;
+    if (B) ora_ephem_eval(m, tn, rb);
+    double f0[42];
+    ora_f_var(m, rb, y, f0);
+    for (int i = 0; i < s; i++)
+      for (int q = 0; q < 42; q++) Kst[i][q] = f0[q];
+    int it;
+    for (it = 0; it < 200; it++) {
+      double chg = 0.0, scl = 0.0;
+      for (int i = 0; i < s; i++) {
+        for (int q = 0; q < 42; q++) {
+          double acc = 0.0;
+          for (int j = 0; j < s; j++) acc += A[i * s + j] * Kst[j][q];
+          ys[q] = y[q] + h * acc;
+        }
+        if (B) ora_ephem_eval(m, tn + c[i] * h, rb);
+        ora_f_var(m, rb, ys, Kn[i]);
+      }
+      for (int i = 0; i < s; i++)
+        for (int q = 0; q < 42; q++) {
+          double d = fabs(Kn[i][q] - Kst[i][q]);
+          if (d > chg) chg = d;
+          if (fabs(Kn[i][q]) > scl) scl = fabs(Kn[i][q]);
+          Kst[i][q] = Kn[i][q];
+        }
+      if (chg <= 1e-17 * scl) break;
+    }
+    if (it == 200) capped++;
+    for (int q = 0; q < 42; q++) {
+      double acc = 0.0;
+      for (int j = 0; j < s; j++) acc += b[j] * Kst[j][q];
+      y[q] = y[q] + h * acc;
+    }
+  }
+  for (int q = 0; q < 6; q++) xf[q] = y[q];
+  for (int i = 0; i < 36; i++) Phi[i] = y[6 + i];
+  free(rb); free(Kst); free(Kn);
+  return capped;
+}
+
+/* ------------------------------------------------------------------ */
+/* b-plane coordinates of a flyby (the paper cites Valsecchi's b-plane   */
+/* for close approaches and prints no formula).  From the planet-relative */
+/* state rel = (r, v) and the planet's GM mu:                            */
+/*   h = r x v,  e_vec = ((v^2 - mu/|r|) r - (r.v) v)/mu,  e = |e_vec|,  */
+/*   P = e_vec/e,  Q = (h/|h|) x P,                                       */
+/*   S = P/e + sqrt(e^2 - 1)/e Q   (direction of the incoming asymptote), */
+/*   T = S x z / |S x z|  (z = (0, 0, 1), the pole of the reference plane),*/
+/*   R = S x T,  B = S x h / v_inf,  v_inf = sqrt(v^2 - 2 mu/|r|),         */
+/* and out = (B.T, B.R).  Returns 1 (out = 0) if the orbit is not         */
+/* hyperbolic.                                                            */
+/* ------------------------------------------------------------------ */
+static void ora_cross(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+int ora_bplane(double mu, const double rel[6], double out[2]) {
+  const double *r = rel, *v = rel + 3;
+  out[0] = out[1] = 0.0;
+  double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double rv = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
+  double vinf2 = v2 - 2.0 * mu / rn;
+  if (!(vinf2 > 0.0)) return 1;
+  double vinf = sqrt(vinf2);
+  double h[3], ev[3], P[3], Q[3], S[3], T[3], R[3], Bv[3], hh[3];
+  ora_cross(r, v, h);
+  double hn = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+  for (int i = 0; i < 3; i++) ev[i] = ((v2 - mu / rn) * r[i] - rv * v[i]) / mu;
+  double e = sqrt(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
+  if (!(e > 1.0)) return 1;
+  for (int i = 0; i < 3; i++) { P[i] = ev[i] / e; hh[i] = h[i] / hn; }
+  ora_cross(hh, P, Q);
+  double se = sqrt(e * e - 1.0) / e;
+  for (int i = 0; i < 3; i++) S[i] = P[i] / e + se * Q[i];
+  const double z[3] = {0.0, 0.0, 1.0};
+  ora_cross(S, z, T);
+  double tn = sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+  for (int i = 0; i < 3; i++) T[i] /= tn;
+  ora_cross(S, T, R);
+  ora_cross(S, h, Bv);
+  for (int i = 0; i < 3; i++) Bv[i] /= vinf;
+  out[0] = Bv[0] * T[0] + Bv[1] * T[1] + Bv[2] * T[2];
+  out[1] = Bv[0] * R[0] + Bv[1] * R[1] + Bv[2] * R[2];
+  return 0;
 }

@@ -281,6 +281,41 @@ def config3(M: int = 65536, seed: int = 3) -> Workload:
 
 
 # --------------------------------------------------------------------------
+# Config 4: differentiation -- config-1 system, one Venus flyby per arc
+# --------------------------------------------------------------------------
+def config4(M: int = 1024, seed: int = 4) -> Workload:
+    """Config-1 system (Sun + Venus + Earth, circular coplanar).  Every IC
+    starts 2-5 days before periapsis of a close Venus flyby (periapsis
+    1e4-5e4 km, v_inf 3-6 km/s, random geometry, taken on the Venus-relative
+    hyperbola) and is propagated for one config-1 revolution; N = 128, 16 base
+    segments per osculating period with halving.  meta["t_ca"] holds each
+    IC's nominal periapsis epoch (where its b-plane is taken), meta["body"]
+    the flyby body's index and meta["mu_body"] its GM."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    names, bodies = _circular_system()
+    a = 0.75 * AU
+    T = 2.0 * np.pi * np.sqrt(a**3 / MU_SUN)
+    t0, tf = 0.0, T
+    tb, ng = _table_span(t0, tf)
+    coef = fit_tables(bodies, tb, ng)
+    venus = bodies[names.index("venus")]
+    rp = rng.uniform(1e4, 5e4, M)
+    vinf = rng.uniform(3.0, 6.0, M)
+    dtp = rng.uniform(2.0, 5.0, M) * DAY
+    x0 = np.zeros((M, 6))
+    vr, vv = venus.state(np.zeros(1) + t0)
+    for m in range(M):
+        r, v = _hyperbola_state(rng, GM["venus"], rp[m], vinf[m], dtp[m])
+        x0[m, :3] = vr[0] + r
+        x0[m, 3:] = vv[0] + v
+    return Workload(f"cfg4_sun_venus_earth_{M}ic_venus_flyby_1rev_N128", MU_SUN, names,
+                    np.array([GM[n] for n in names]), tb, GRANULE, coef, x0, t0, tf, N=128, segments=16,
+                    seg_mode=1, tol=1e-13, max_iters=60, max_depth=12,
+                    meta=dict(seed=seed, rp_km=rp, vinf_kms=vinf, t_ca=t0 + dtp, body=names.index("venus"),
+                              mu_body=GM["venus"], revolution_s=T))
+
+
+# --------------------------------------------------------------------------
 # Config 5: uneven batching -- per-trajectory durations, degrees and segments
 # --------------------------------------------------------------------------
 # Segments per revolution of the config-1 orbit at which the oracle converges to
