@@ -248,6 +248,77 @@ pc_status pc_propagate_groups(pc_plan *const *plans, int n_groups, const long lo
                               const double *t0, const double *tf, const int *segments, double tol, double *xf,
                               int *status, int *iters, int *nseg, long long *rounds, void *stream);
 
+/* ---- Reverse mode ----------------------------------------------------------
+ * Gradients of the final state with respect to the initial state, through the
+ * converged PC fixed point of every segment (the paper stops at the forward
+ * propagation; its Conclusions name optimisation over the propagated states as
+ * the use).  For a segment with converged nodes Y = 1 x0^T + omega2 K G(Y), a
+ * cotangent ybar on its end state y_N gives
+ *   x0bar = sum_j lambda_j,   lambda = Ybar + J^T (omega2 K^T lambda),
+ * Ybar = ybar at node N, J = blockdiag(df/dy at the nodes); the linear adjoint
+ * equation is swept like the forward one, from the last segment back.  The
+ * segment schedule (including halvings) is held fixed: the result is the
+ * derivative of the discrete map x0 -> xf that the forward pass computed. */
+
+/* Forward pass that also records the tape the reverse sweep needs: for each
+ * trajectory i and accepted segment k < max_seg, a record of 2 + 6(N+1)
+ * doubles at tape[(i * max_seg + k) * (2 + 6(N+1))]:
+ *   (t_a, t_b, y_0[6], y_1[6], ..., y_N[6])   -- the segment's converged nodes.
+ *   x0, xf      device, planar [6][n_ic]
+ *   t0, tf      device [n_ic], each trajectory's arc (tf < t0 backward)
+ *   segments    device [n_ic] base segment counts, or NULL (the plan's)
+ *   status      device [n_ic] PC_IC_* bits, or NULL
+ *   nseg        device [n_ic], required: accepted segments (may exceed max_seg,
+ *               in which case the tape misses the later ones and
+ *               pc_adjoint_tape refuses it)
+ *   tape        device, n_ic * max_seg * (2 + 6(N+1)) doubles, max_seg >= 1
+ * Same rules and results as pc_propagate otherwise.  Returns PC_OK,
+ * PC_ENOTCONV, PC_EINVAL, PC_ENOMEM or PC_ECUDA. */
+pc_status pc_propagate_tape(pc_plan *plan, long long n_ic, const double *x0, const double *t0, const double *tf,
+                            const int *segments, double tol, double *xf, int *status, int *nseg, int max_seg,
+                            double *tape, void *stream);
+
+/* Reverse sweep over a tape: x0_bar = (d xf / d x0)^T xf_bar per trajectory.
+ *   nseg, tape   as written by pc_propagate_tape with the same plan and max_seg
+ *   xf_bar       device, planar [6][n_ic], read only
+ *   tol          stopping tolerance of the adjoint sweeps (<= 0: the plan's);
+ *                the plan's stall rule applies, with twice its sweep cap
+ *   x0_bar       device, planar [6][n_ic], written (may alias xf_bar)
+ *   status       device [n_ic] or NULL: PC_IC_STALLED / NOT_CONVERGED / NONFINITE
+ *                bits of the adjoint sweeps
+ *   iters        device [n_ic] or NULL: adjoint sweeps spent
+ * The call copies nseg to the host (it synchronizes `stream`) to order the
+ * trajectories by segment count.  Returns PC_OK, PC_ENOTCONV (an adjoint
+ * sweep hit its cap or blew up), PC_EINVAL (a count above max_seg, or a degree
+ * whose tile does not fit in shared memory), PC_ENOMEM or PC_ECUDA. */
+pc_status pc_adjoint_tape(pc_plan *plan, long long n_ic, const int *nseg, int max_seg, const double *tape,
+                          const double *xf_bar, double tol, double *x0_bar, int *status, int *iters, void *stream);
+
+/* Forward pass with a tape held by the plan, then the reverse sweep:
+ * x0_bar = (d xf / d x0)^T xf_bar for the arc [t0, tf].  Device buffers,
+ * planar [6][n_ic].  The tape (n_ic x segments x (2 + 6(N+1)) doubles) is
+ * grown and the forward pass rerun if a trajectory needed more segments than
+ * it had room for.  Synchronizes `stream`.  Returns PC_OK, PC_ENOTCONV,
+ * PC_EINVAL, PC_ENOMEM or PC_ECUDA. */
+pc_status pc_propagate_adjoint(pc_plan *plan, long long n_ic, const double *x0, double t0, double tf, double tol,
+                               const double *xf_bar, double *x0_bar, void *stream);
+
+/* b-plane coordinates (B.T, B.R) of n flybys of body `body` (index into the
+ * plan's ephemeris, GM mu_body) at times t [n] from heliocentric states x
+ * (planar [6][n]); the paper cites the b-plane without a formula.  With
+ * rel = x - (r_b(t), v_b(t)) (body velocity = time derivative of its table
+ * series), h = r x v, e_vec = ((v^2 - mu/|r|) r - (r.v) v)/mu, P = e_vec/e,
+ * Q = (h/|h|) x P, incoming asymptote S = P/e + sqrt(e^2-1)/e Q,
+ * T = S x z/|S x z| (z = (0,0,1)), R = S x T, B = S x h/v_inf.
+ *   out      device planar [2][n] (B.T, B.R), or NULL
+ *   jac      device planar [12][n]: d out_k / d x_q at row 6k + q, or NULL
+ *   out_bar, x_bar   device planar [2][n] and [6][n]: x_bar = J^T out_bar
+ *            (both or neither)
+ * Forward-mode derivatives (exact to rounding).  A state that is not
+ * hyperbolic with respect to the body gives NaN and PC_ENONFINITE. */
+pc_status pc_bplane(pc_plan *plan, int body, double mu_body, long long n, const double *t, const double *x,
+                    double *out, double *jac, const double *out_bar, double *x_bar, void *stream);
+
 /* Copies the plan's operator K ((N+1) x (N+1), row-major) and nodes tau (N+1)
  * to host buffers (either may be NULL).  For tests and diagnostics. */
 pc_status pc_plan_operator(const pc_plan *plan, double *K, double *tau);

@@ -45,7 +45,7 @@ struct Arcs {
 
 pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld, long long io_off, const double *x0,
                         const Arcs &arcs, double tol, double *xf, int *status, int *iters, int *nseg, int max_ckpt,
-                        double *ckpt, cudaStream_t st) {
+                        double *ckpt, int tape_seg, double *tape, cudaStream_t st) {
   const pc_options &o = p->opt;
   const int mixed = o.precision == PC_PREC_MIXED ? 1 : 0;
   pc_status ps = ensure_workspace(p, n_ic, mixed);
@@ -79,6 +79,8 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   s.trunc_tol = o.trunc_tol;
   s.max_ckpt = max_ckpt;
   s.ckpt = max_ckpt > 0 ? ckpt : nullptr;
+  s.tape_seg = tape_seg;
+  s.tape = tape_seg > 0 ? tape : nullptr;
   s.xf = xf;
   s.status = status;
   s.iters = iters;
@@ -204,12 +206,28 @@ extern "C" pc_status pc_propagate_ex(pc_plan *p, long long n_ic, const double *x
   }
   Session S;
   const Arcs arcs{t0, tf, nullptr, nullptr, nullptr};
-  pc_status ps = session_begin(S, p, n_ic, n_ic, 0, x0, arcs, tol, xf, status, iters, nseg, max_ckpt, ckpt,
-                               (cudaStream_t)stream);
+  pc_status ps = session_begin(S, p, n_ic, n_ic, 0, x0, arcs, tol, xf, status, iters, nseg, max_ckpt, ckpt, 0,
+                               nullptr, (cudaStream_t)stream);
   if (ps != PC_OK) return ps;
   while (!S.finished && S.e == cudaSuccess) session_step(S);
   return session_finish(S, rounds_out);
 }
+
+namespace pcx {
+// One-group propagation with per-trajectory or scalar arcs that records the
+// adjoint tape (pc_adjoint.cu).
+pc_status propagate_with_tape(pc_plan *p, long long n_ic, const double *x0, double t0s, double tfs,
+                              const double *t0a, const double *tfa, const int *sega, double tol, double *xf,
+                              int *status, int *iters, int *nseg, int tape_seg, double *tape, cudaStream_t st) {
+  Session S;
+  const Arcs arcs{t0s, tfs, t0a, tfa, sega};
+  pc_status ps = session_begin(S, p, n_ic, n_ic, 0, x0, arcs, tol, xf, status, iters, nseg, 0, nullptr, tape_seg,
+                               tape, st);
+  if (ps != PC_OK) return ps;
+  while (!S.finished && S.e == cudaSuccess) session_step(S);
+  return session_finish(S, nullptr);
+}
+}  // namespace pcx
 
 extern "C" pc_status pc_propagate(pc_plan *p, long long n_ic, const double *x0, double t0, double tf, double tol,
                                   double *xf, int *status, int *iters, void *stream) {
@@ -248,7 +266,7 @@ extern "C" pc_status pc_propagate_groups(pc_plan *const *plans, int n_groups, co
       if (e != cudaSuccess) break;
       const Arcs arcs{0.0, 0.0, t0, tf, segments};
       pc_status ps = session_begin(S[g], p, counts[g], total, off, x0, arcs, tol, xf, status, iters, nseg, 0,
-                                   nullptr, p->own_stream);
+                                   nullptr, 0, nullptr, p->own_stream);
       if (ps != PC_OK) {
         result = ps;
         S[g].finished = true;

@@ -72,6 +72,10 @@ struct Sweep {
   double switch_tol;         // FP32 -> FP64 when the FP32 change is below this
   int max_ckpt;
   double *ckpt;              // [n_ic][max_ckpt][7] or nullptr
+  // adjoint checkpoints: per trajectory and accepted segment k < tape_seg a record
+  // (t_a, t_b, y_j[6] for j = 0..N) of tape_rec() doubles, or nullptr
+  int tape_seg;
+  double *tape;              // [n_ic][tape_seg][2 + 6n]
   // outputs, indexed by trajectory, written when a trajectory finishes
   double *xf;                // [6][n_ic]
   int *status, *iters, *nseg;
@@ -113,6 +117,20 @@ struct Workspace {
 
 }  // namespace pcx
 
+// Reverse-sweep workspace (pc_adjoint.cu).
+struct AdjWorkspace {
+  long long cap = 0;
+  int *perm = nullptr;       // [cap] trajectories by segment count, descending
+  double *xb = nullptr;      // [6][cap] running cotangent
+  double *xf = nullptr;      // [6][cap] forward result of pc_propagate_adjoint
+  int *nseg = nullptr;       // [cap]
+  int *fail = nullptr;       // [1]
+  int *h_fail = nullptr;     // pinned
+  double *tape = nullptr;    // pc_propagate_adjoint's own tape
+  size_t tape_bytes = 0;
+  int tape_hint = 0;         // segment capacity that sufficed last time
+};
+
 struct pc_plan {
   int N = 0, n = 0, kpad = 0, rows_pad = 0;
   int segments = 0;
@@ -130,6 +148,13 @@ struct pc_plan {
   double *h_K = nullptr;     // host copy, (N+1) x (N+1)
   double *h_tau = nullptr;   // [n]
   pcx::Workspace ws;
+  // adjoint: the operator transposed without its zero row, KTp[j][k'] = K[k'+1][j]
+  // (j < N+1, k' < N), zero-padded to adj_mpad = 16 ceil((N+1)/16) rows and
+  // adj_kpad = 4 ceil(N/4) columns
+  double *d_KTp = nullptr;
+  int adj_mpad = 0, adj_kpad = 0;
+  int num_sms = 0;
+  AdjWorkspace adj;
   // per-kernel timing: 6 events per recorded round (before setup, force,
   // contract, the FP32 kernels, control, after control)
   cudaStream_t own_stream = nullptr;  // created for multi-group calls
@@ -144,6 +169,13 @@ namespace pcx {
 // pc_plan.cu
 pc_status ensure_workspace(pc_plan *plan, long long n_ic, int mixed);
 void free_workspace(pc_plan *plan);
+// pc_adjoint.cu
+void free_adjoint_workspace(pc_plan *plan);
+// pc_api.cu
+pc_status propagate_with_tape(pc_plan *p, long long n_ic, const double *x0, double t0s, double tfs,
+                              const double *t0a, const double *tfa, const int *sega, double tol, double *xf,
+                              int *status, int *iters, int *nseg, int tape_seg, double *tape, cudaStream_t st);
+__host__ __device__ inline int tape_rec(int n) { return 2 + 6 * n; }
 // pc_sweep.cu
 cudaError_t launch_init(const pc_plan *plan, const Sweep &s, const double *x0, cudaStream_t st);
 cudaError_t launch_round(const pc_plan *plan, const Sweep &s, int cur, cudaStream_t st,

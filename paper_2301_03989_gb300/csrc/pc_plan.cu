@@ -150,6 +150,17 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
     if (e == cudaSuccess) e = dalloc(&p->d_K32T, Kt.size());
     if (e == cudaSuccess) e = cudaMemcpy(p->d_K32T, Kt.data(), sizeof(float) * Kt.size(), cudaMemcpyHostToDevice);
   }
+  // Adjoint operator: K transposed without its zero row 0, KTp[j][k'] = K[k'+1][j].
+  p->adj_mpad = (n + 15) / 16 * 16;
+  p->adj_kpad = (N + 3) / 4 * 4;
+  {
+    std::vector<double> KT((size_t)p->adj_mpad * p->adj_kpad, 0.0);
+    for (int j = 0; j < n; j++)
+      for (int k = 0; k < N; k++) KT[(size_t)j * p->adj_kpad + k] = p->h_K[(size_t)(k + 1) * n + j];
+    if (e == cudaSuccess) e = dalloc(&p->d_KTp, KT.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_KTp, KT.data(), sizeof(double) * KT.size(), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e == cudaSuccess) e = dalloc(&p->d_tau, n);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_tau, p->h_tau, sizeof(double) * n, cudaMemcpyHostToDevice);
   Model &m = p->model;
@@ -289,9 +300,11 @@ void pcx::free_workspace(pc_plan *p) {
 extern "C" void pc_plan_destroy(pc_plan *p) {
   if (!p) return;
   free_workspace(p);
+  free_adjoint_workspace(p);
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   if (p->own_stream) cudaStreamDestroy(p->own_stream);
   cudaFree(p->d_K);
+  cudaFree(p->d_KTp);
   cudaFree(p->d_K32T);
   cudaFree(p->d_tau);
   cudaFree(p->d_mu);

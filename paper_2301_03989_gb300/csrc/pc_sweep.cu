@@ -23,28 +23,11 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "pc_device.cuh"
 #include "pc_internal.h"
 
 namespace pcx {
 namespace {
-
-__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
-
-// NaN-propagating maximum of non-negative values.
-__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
-__device__ __forceinline__ float nanmaxf(float a, float b) { return (b > a || b != b) ? b : a; }
-
-// Non-negative doubles / floats order like their bit patterns; NaN maps to the largest.
-__device__ __forceinline__ unsigned long long err_bits(double e) {
-  if (e != e) return 0x7FF8000000000000ULL;
-  return (unsigned long long)__double_as_longlong(e);
-}
-__device__ __forceinline__ unsigned err_bits32(float e) {
-  if (e != e) return 0x7FC00000u;
-  return __float_as_uint(e);
-}
 
 // Warp-aggregated append of `flag` lanes to list[] with counter *cnt.  Every
 // lane of the warp must call it.
@@ -163,40 +146,6 @@ __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, 
     }
   }
   warp_append(to64, m, s.l64[s.list_cur], s.l64_cnt + s.list_cur);
-}
-
-// ---------------------------------------------------------------------------
-// Ephemeris: Clenshaw evaluation of body b at time t,
-//   b_k = c_k + 2 sigma b_{k+1} - b_{k+2},  r = c_0 + sigma b_1 - b_2.
-// Every operation is rounded on its own (no fused multiply-add), so the body
-// positions are the exactly rounded results of this recurrence: near a body
-// the force amplifies a position rounding difference by |r| / |r - r_b|.
-// ---------------------------------------------------------------------------
-struct EphemLoc {
-  int g;
-  double sig;
-};
-
-__device__ __forceinline__ EphemLoc ephem_locate(const Model &md, double t) {
-  int g = (int)floor((t - md.t_begin) / md.granule);
-  g = g < 0 ? 0 : (g > md.n_gr - 1 ? md.n_gr - 1 : g);
-  const double tg = dadd(md.t_begin, dmul((double)g, md.granule));
-  return {g, dsub(dmul(2.0, dsub(t, tg)) / md.granule, 1.0)};
-}
-
-__device__ __forceinline__ void ephem_body(const Model &md, EphemLoc L, int b, double r[3]) {
-  const double s2 = dmul(2.0, L.sig);
-  const int nc = md.deg + 1;
-  for (int ax = 0; ax < 3; ax++) {
-    const double *cf = md.coef + (((size_t)b * md.n_gr + L.g) * 3 + ax) * nc;
-    double b1 = 0.0, b2 = 0.0;
-    for (int k = nc - 1; k >= 1; k--) {
-      const double b0 = dsub(dadd(cf[k], dmul(s2, b1)), b2);
-      b2 = b1;
-      b1 = b0;
-    }
-    r[ax] = dsub(dadd(cf[0], dmul(L.sig, b1)), b2);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -451,13 +400,6 @@ __global__ void __launch_bounds__(32 * kForceNodes) k_force(Sweep s, Ctl c, Mode
 // c2,c3 = C[g+8][2t..2t+1].  Epilogue: Y' = x0 + acc and (unless DIAG) the
 // per-trajectory maximum change, reduced over the warp, merged with atomicMax.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void dmma16x8x4(double (&d)[4], double a0, double a1, double b0) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
-      : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
-      : "d"(a0), "d"(a1), "d"(b0));
-}
-
 // One CTA of kSplit warps computes one tile; warp w accumulates the k-steps
 // [w*ks/kSplit, (w+1)*ks/kSplit) of it (ks = kpad/4 steps of 4), the partial
 // accumulators meet in shared memory and warp 0 adds them in warp order (a
@@ -945,6 +887,13 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
         double *ck = s.ckpt + ((size_t)(s.io_off + c.ic[m]) * s.max_ckpt + k) * 7;
         ck[0] = c.ta[m];
         for (int q = 0; q < 6; q++) ck[1 + q] = c.x[q * ld + m];
+      }
+      if (s.tape && k < s.tape_seg) {
+        double *rec = s.tape + ((size_t)(s.io_off + c.ic[m]) * s.tape_seg + k) * (size_t)tape_rec(s.n);
+        rec[0] = c.ta[m];
+        rec[1] = c.tb[m];
+        for (int j = 0; j < s.n; j++)
+          for (int q = 0; q < 6; q++) rec[2 + 6 * j + q] = Ynew[((size_t)j * 6 + q) * ld + m];
       }
       const size_t last_row = (size_t)s.N * 6 * ld + m;
       for (int q = 0; q < 6; q++) c.x[q * ld + m] = Ynew[last_row + (size_t)q * ld];

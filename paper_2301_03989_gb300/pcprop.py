@@ -25,7 +25,7 @@ PC_PREC_FP64, PC_PREC_MIXED = 0, 1
 EXPORTS = ["pc_options_default", "pc_plan_create", "pc_propagate", "pc_propagate_ex", "pc_eval_ephemeris",
            "pc_eval_dynamics", "pc_eval_warm_start", "pc_apply_operator", "pc_plan_operator", "pc_plan_destroy",
            "pc_status_string", "pc_plan_set_profiling", "pc_plan_kernel_times", "pc_apply_operator_static",
-           "pc_propagate_groups"]
+           "pc_propagate_groups", "pc_propagate_tape", "pc_adjoint_tape", "pc_propagate_adjoint", "pc_bplane"]
 KERNEL_NAMES = ["setup", "fp32", "force", "contract", "control"]
 
 
@@ -78,6 +78,10 @@ def lib():
             L.pc_apply_operator_static.argtypes = [vp, ll, vp, vp, vp, vp]
             L.pc_propagate_groups.argtypes = [C.POINTER(vp), i, C.POINTER(ll), vp, vp, vp, vp, d, vp, vp, vp, vp,
                                               C.POINTER(ll), vp]
+            L.pc_propagate_tape.argtypes = [vp, ll, vp, vp, vp, vp, d, vp, vp, vp, i, vp, vp]
+            L.pc_adjoint_tape.argtypes = [vp, ll, vp, i, vp, vp, d, vp, vp, vp, vp]
+            L.pc_propagate_adjoint.argtypes = [vp, ll, vp, d, d, d, vp, vp, vp]
+            L.pc_bplane.argtypes = [vp, i, d, ll, vp, vp, vp, vp, vp, vp, vp]
             L.pc_plan_operator.argtypes = [vp, vp, vp]
             L.pc_plan_destroy.argtypes = [vp]
             L.pc_plan_destroy.restype = None
@@ -209,6 +213,51 @@ def propagate_groups(plans, counts, x0, t0, tf, xf, segments=None, tol: float = 
                                      _ptr(status), _ptr(iters), _ptr(nseg), C.byref(rounds), _stream(stream))
     _check(code, "pc_propagate_groups", ok=(PC_OK, PC_ENOTCONV))
     return code, int(rounds.value)
+
+
+def tape_record(plan: Plan) -> int:
+    """Doubles per tape record: (t_a, t_b) and the 6 components of the N+1 nodes."""
+    return 2 + 6 * (plan.N + 1)
+
+
+def propagate_tape(plan: Plan, x0, t0, tf, xf, nseg, tape, max_seg: int, segments=None, tol: float = 0.0,
+                   status=None, stream=None) -> int:
+    """Forward pass recording the adjoint tape (device [n_ic * max_seg * tape_record]).
+    t0, tf: device [n_ic] arcs; nseg: device int32 [n_ic].  Returns the pc_status."""
+    n_ic = int(x0.shape[-1])
+    code = lib().pc_propagate_tape(plan.handle, n_ic, _ptr(x0), _ptr(t0), _ptr(tf), _ptr(segments), float(tol),
+                                   _ptr(xf), _ptr(status), _ptr(nseg), int(max_seg), _ptr(tape), _stream(stream))
+    _check(code, "pc_propagate_tape", ok=(PC_OK, PC_ENOTCONV))
+    return code
+
+
+def adjoint_tape(plan: Plan, nseg, max_seg: int, tape, xf_bar, x0_bar, tol: float = 0.0, status=None, iters=None,
+                 stream=None) -> int:
+    """Reverse sweep: x0_bar = (d xf / d x0)^T xf_bar (planar [6][n_ic])."""
+    n_ic = int(xf_bar.shape[-1])
+    code = lib().pc_adjoint_tape(plan.handle, n_ic, _ptr(nseg), int(max_seg), _ptr(tape), _ptr(xf_bar), float(tol),
+                                 _ptr(x0_bar), _ptr(status), _ptr(iters), _stream(stream))
+    _check(code, "pc_adjoint_tape", ok=(PC_OK, PC_ENOTCONV))
+    return code
+
+
+def propagate_adjoint(plan: Plan, x0, t0: float, tf: float, xf_bar, x0_bar, tol: float = 0.0, stream=None) -> int:
+    n_ic = int(x0.shape[-1])
+    code = lib().pc_propagate_adjoint(plan.handle, n_ic, _ptr(x0), float(t0), float(tf), float(tol), _ptr(xf_bar),
+                                      _ptr(x0_bar), _stream(stream))
+    _check(code, "pc_propagate_adjoint", ok=(PC_OK, PC_ENOTCONV))
+    return code
+
+
+def bplane(plan: Plan, body: int, mu_body: float, t, x, out=None, jac=None, out_bar=None, x_bar=None,
+           stream=None) -> int:
+    """b-plane (B.T, B.R) planar [2][n] of states x (planar [6][n]) at times t [n];
+    jac planar [12][n]; x_bar = J^T out_bar."""
+    n = int(x.shape[-1])
+    code = lib().pc_bplane(plan.handle, int(body), float(mu_body), n, _ptr(t), _ptr(x), _ptr(out), _ptr(jac),
+                           _ptr(out_bar), _ptr(x_bar), _stream(stream))
+    _check(code, "pc_bplane", ok=(PC_OK, PC_ENONFINITE))
+    return code
 
 
 def eval_ephemeris(plan: Plan, t, rb, stream=None):
