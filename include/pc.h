@@ -226,6 +226,44 @@ pc_status pc_plan_set_profiling(pc_plan *plan, int on);
  * the previous pc_plan_kernel_times, whether profiling was on or not. */
 pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
 
+/* ---- Launch tuning and CUDA graphs ------------------------------------------
+ * Launch shapes of the sweep kernels and the host's round loop.  None of them
+ * changes any arithmetic: results are bitwise the same for every setting.
+ *   setup_ctas_per_sm     CTAs per SM of the new-segment set-up kernel (1..16)
+ *   fp32_ctas_per_sm      CTAs per SM of the FP32 warp kernel (1..8)
+ *   contract_ctas_per_sm  persistent CTAs per SM of the FP64 contraction (1..16)
+ *   rounds_per_batch      sweep rounds queued between two looks at the device's
+ *                         done counter (1..64)
+ *   repack_div            compact the working set when at least 1/repack_div of
+ *                         its slots have finished (2..64)
+ *   graphs                1: each batch of rounds is captured once per working-set
+ *                         shape as a CUDA graph and replayed (0: direct launches)
+ * Defaults: 4, 2, 4, 8, 8, 1.  Profiling (pc_plan_set_profiling) launches
+ * directly whatever `graphs` says. */
+typedef struct {
+  int setup_ctas_per_sm;
+  int fp32_ctas_per_sm;
+  int contract_ctas_per_sm;
+  int rounds_per_batch;
+  int repack_div;
+  int graphs;
+} pc_tuning;
+
+/* Reads / replaces the plan's tuning (PC_EINVAL on a value out of range). */
+pc_status pc_plan_get_tuning(const pc_plan *plan, pc_tuning *out);
+pc_status pc_plan_set_tuning(pc_plan *plan, const pc_tuning *t);
+
+/* Autotuner: coordinate descent over the tuning fields (contraction CTAs,
+ * set-up CTAs, FP32 CTAs, rounds per batch, compaction threshold, graphs), each
+ * candidate timed with CUDA events on a propagation of the caller's
+ * trajectories x0 (device, planar [6][n_ic]) over [t0, tf] capped at
+ * max_rounds sweep rounds (>= 16).  The fastest setting per round is kept in
+ * the plan and copied to *best (may be NULL).  Allocates its own scratch
+ * outputs; synchronizes `stream`.  Returns PC_OK, PC_EINVAL, PC_ENOMEM or
+ * PC_ECUDA. */
+pc_status pc_plan_autotune(pc_plan *plan, long long n_ic, const double *x0, double t0, double tf, int max_rounds,
+                           pc_tuning *best, void *stream);
+
 /* Uneven batching: n_groups groups of trajectories, group g propagated with
  * plans[g] (its own degree N, segment count and options) -- the paper's
  * two-level augmentation (Section "Two-level augmentation") with the outer

@@ -1,4 +1,5 @@
 // Host driver of the batched sweep and the kernel-level entry points.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -13,11 +14,6 @@ pc_status cuda_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
 }
 
-// Rounds issued between two looks at the done counter.  The host keeps one
-// batch in flight while it waits for the previous batch's counter, so the GPU
-// does not idle during the check.
-constexpr int kRoundsPerBatch = 8;
-
 }  // namespace
 
 namespace {
@@ -30,7 +26,9 @@ namespace {
 struct Session {
   pc_plan *p = nullptr;
   Sweep s{};
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;      // where the rounds run
+  cudaStream_t caller = nullptr;  // the caller's stream, when st is the plan's own
+  bool forked = false;
   cudaError_t e = cudaSuccess;
   long long n_ic = 0, rounds = 0, max_rounds = 0;
   int cur = 0, pending = -1, done_known = 0;
@@ -100,6 +98,21 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   w.live = 0;
   S.p = p;
   S.st = st;
+  S.caller = st;
+  S.forked = false;
+  // A default stream cannot be captured into a graph: run on the plan's own
+  // stream, ordered after the caller's work by an event (joined back at finish).
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) {
+    cudaError_t e = cudaSuccess;
+    if (!p->own_stream) e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->fork_ev) e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(p->fork_ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->own_stream, p->fork_ev, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    S.st = p->own_stream;
+    S.forked = true;
+  }
+  st = S.st;
   S.n_ic = n_ic;
   S.rounds = 0;
   S.max_rounds = o.max_rounds > 0 ? o.max_rounds : 10000000LL;
@@ -107,8 +120,54 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   S.pending = -1;
   S.done_known = 0;
   S.finished = S.capped = false;
-  S.e = launch_init(p, s, x0, st);
+  p->session_id += 1;  // a new call: kernel arguments differ, no cached graph applies
+  S.e = prepare_launches(p);
+  if (S.e == cudaSuccess) S.e = launch_init(p, s, x0, st);
   return S.e == cudaSuccess ? PC_OK : cuda_status(S.e);
+}
+
+// One batch of R rounds as a CUDA graph.  The rounds' kernel arguments depend
+// only on the call, the working-set size and the buffer parities, so the graph
+// is captured once per (call, A, parities) and replayed until a compaction
+// changes them.
+cudaError_t run_batch_graph(Session &S, int R) {
+  pc_plan *p = S.p;
+  Workspace &w = p->ws;
+  Sweep &s = S.s;
+  const long long key[5] = {p->session_id, s.A, S.cur, s.list_cur, (long long)w.live * 1024 + R};
+  cudaError_t e = cudaSuccess;
+  if (!w.graph || !std::equal(key, key + 5, w.graph_key)) {
+    if (w.graph) {
+      cudaGraphExecDestroy(w.graph);
+      w.graph = nullptr;
+    }
+    e = cudaStreamBeginCapture(S.st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const long long l0 = p->acc_launches;
+    Sweep sc = s;
+    int cc = S.cur;
+    cudaError_t le = cudaSuccess;
+    for (int r = 0; r < R && le == cudaSuccess; r++) {
+      le = launch_round(p, sc, cc, S.st, nullptr);
+      cc ^= 1;
+      sc.list_cur ^= 1;
+    }
+    w.graph_launches = p->acc_launches - l0;
+    p->acc_launches = l0;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(S.st, &g);
+    if (e == cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&w.graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      w.graph = nullptr;
+      return e;
+    }
+    std::copy(key, key + 5, w.graph_key);
+  }
+  e = cudaGraphLaunch(w.graph, S.st);
+  p->acc_launches += w.graph_launches;
+  return e;
 }
 
 void session_step(Session &S) {
@@ -117,7 +176,14 @@ void session_step(Session &S) {
   Sweep &s = S.s;
   Workspace &w = p->ws;
   cudaError_t &e = S.e;
-  for (int r = 0; r < kRoundsPerBatch && e == cudaSuccess && s.A > 0; r++) {
+  const int R = p->tune.rounds_per_batch;
+  if (p->tune.graphs && !p->prof_on && (R % 2) == 0 && s.A > 0) {
+    // replay: an even number of rounds returns both parities to where they were
+    e = run_batch_graph(S, R);
+    S.rounds += R;
+  }
+  for (int r = 0; r < R && e == cudaSuccess && s.A > 0 && !(p->tune.graphs && !p->prof_on && (R % 2) == 0);
+       r++) {
     cudaEvent_t *ev = nullptr;
     if (p->prof_on) {
       const size_t need = (size_t)(p->prof_rounds + 1) * 6;
@@ -153,11 +219,12 @@ void session_step(Session &S) {
     S.finished = true;
     return;
   }
-  // Compaction: when at least 1/8 of the slots hold finished trajectories,
-  // move the active ones to the front so later rounds launch over fewer slots.
+  // Compaction: when at least 1/repack_div of the slots hold finished trajectories,
+  // move the active ones to the front so later rounds launch over fewer slots
+// (with the default repack_div of 8).
   const long long active = S.n_ic - S.done_known;
   const long long dead = (long long)s.A - active;
-  if (dead > 0 && dead * 8 >= (long long)s.A) {
+  if (dead > 0 && dead * p->tune.repack_div >= (long long)s.A) {
     e = launch_repack(p, s, S.cur, S.st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ints + 16, w.ints + 4, sizeof(int), cudaMemcpyDeviceToHost, S.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
@@ -180,6 +247,10 @@ pc_status session_finish(Session &S, long long *rounds_out) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w.h_cnt64, w.cnt64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, S.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
+  if (e == cudaSuccess && S.forked) {
+    e = cudaEventRecord(p->fork_ev, S.st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S.caller, p->fork_ev, 0);
+  }
   if (rounds_out) *rounds_out += S.rounds;
   if (e != cudaSuccess) return cuda_status(e);
   p->acc_sweeps64 += (long long)w.h_cnt64[0];
@@ -369,4 +440,90 @@ extern "C" pc_status pc_plan_kernel_times(pc_plan *p, pc_kernel_times *out) {
   p->acc_sweeps64 = p->acc_sweeps32 = 0;
   p->acc_launches = 0;
   return cuda_status(e);
+}
+
+extern "C" pc_status pc_plan_get_tuning(const pc_plan *p, pc_tuning *out) {
+  if (!p || !out) return PC_EINVAL;
+  *out = p->tune;
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_set_tuning(pc_plan *p, const pc_tuning *t) {
+  if (!p || !t) return PC_EINVAL;
+  if (t->setup_ctas_per_sm < 1 || t->setup_ctas_per_sm > 16 || t->fp32_ctas_per_sm < 1 || t->fp32_ctas_per_sm > 8 ||
+      t->contract_ctas_per_sm < 1 || t->contract_ctas_per_sm > 16 || t->rounds_per_batch < 1 ||
+      t->rounds_per_batch > 64 || t->repack_div < 2 || t->repack_div > 64 || (t->graphs != 0 && t->graphs != 1))
+    return PC_EINVAL;
+  p->tune = *t;
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_autotune(pc_plan *p, long long n_ic, const double *x0, double t0, double tf,
+                                      int max_rounds, pc_tuning *best, void *stream) {
+  if (!p || n_ic < 1 || !x0 || max_rounds < 16 || n_ic > (1LL << 30)) return PC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *xf = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaMalloc((void **)&xf, sizeof(double) * 6 * (size_t)n_ic);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  const long long saved_rounds = p->opt.max_rounds;
+  const int saved_prof = p->prof_on;
+  p->opt.max_rounds = max_rounds;
+  p->prof_on = 0;
+  pc_status ps = PC_OK;
+  // time per round of a propagation capped at max_rounds with tuning t
+  auto trial = [&](const pc_tuning &t, double *ms_per_round) -> pc_status {
+    p->tune = t;
+    if ((e = cudaEventRecord(ev[0], st)) != cudaSuccess) return cuda_status(e);
+    long long rounds = 0;
+    pc_status r = pc_propagate_ex(p, n_ic, x0, t0, tf, 0.0, xf, nullptr, nullptr, nullptr, 0, nullptr, &rounds, st);
+    if (r != PC_OK && r != PC_ENOTCONV) return r;
+    if ((e = cudaEventRecord(ev[1], st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaEventSynchronize(ev[1])) != cudaSuccess) return cuda_status(e);
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, ev[0], ev[1])) != cudaSuccess) return cuda_status(e);
+    *ms_per_round = rounds > 0 ? ms / (double)rounds : 1e30;
+    return PC_OK;
+  };
+  pc_tuning cur = p->tune;
+  double cur_ms = 0.0;
+  if (e != cudaSuccess) ps = cuda_status(e);
+  if (ps == PC_OK) ps = trial(cur, &cur_ms);  // warm-up: workspace allocation, first captures
+  if (ps == PC_OK) ps = trial(cur, &cur_ms);
+  const bool mixed = p->opt.precision == PC_PREC_MIXED;
+  struct Axis {
+    int pc_tuning::*field;
+    std::vector<int> values;
+  };
+  const std::vector<Axis> axes = {
+      {&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8}},
+      {&pc_tuning::setup_ctas_per_sm, {2, 4, 8}},
+      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{}},
+      {&pc_tuning::rounds_per_batch, {4, 8, 16, 32}},
+      {&pc_tuning::repack_div, {4, 8, 16}},
+      {&pc_tuning::graphs, {0, 1}},
+  };
+  for (const Axis &ax : axes) {
+    for (int v : ax.values) {
+      if (ps != PC_OK) break;
+      if (cur.*(ax.field) == v) continue;
+      pc_tuning cand = cur;
+      cand.*(ax.field) = v;
+      double ms = 0.0;
+      ps = trial(cand, &ms);
+      if (ps == PC_OK && ms < 0.99 * cur_ms) {  // keep a change only for a clear gain
+        cur = cand;
+        cur_ms = ms;
+      }
+    }
+  }
+  p->tune = cur;
+  p->opt.max_rounds = saved_rounds;
+  p->prof_on = saved_prof;
+  if (best) *best = cur;
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  cudaFree(xf);
+  return ps;
 }

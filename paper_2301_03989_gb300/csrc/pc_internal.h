@@ -111,6 +111,10 @@ struct Workspace {
   unsigned long long *h_cnt64 = nullptr;
   int *h_ints = nullptr;     // pinned host mirror: 2 slots of 8 ints, [16] repack count
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // CUDA graph of one batch of rounds, valid for one (call, working-set shape)
+  cudaGraphExec_t graph = nullptr;
+  long long graph_key[5] = {-1, -1, -1, -1, -1};
+  long long graph_launches = 0;  // kernels per replay
   int live = 0;              // which of E/Aind/ctl/YK/... is live
   int mixed = 0;             // mixed-precision buffers present
 };
@@ -135,6 +139,8 @@ struct pc_plan {
   int N = 0, n = 0, kpad = 0, rows_pad = 0;
   int segments = 0;
   pc_options opt{};
+  pc_tuning tune{4, 2, 4, 8, 8, 1};
+  long long session_id = 0;  // distinguishes calls for the graph cache
   int device = 0;
   // model (device copies)
   pcx::Model model{};
@@ -157,7 +163,8 @@ struct pc_plan {
   AdjWorkspace adj;
   // per-kernel timing: 6 events per recorded round (before setup, force,
   // contract, the FP32 kernels, control, after control)
-  cudaStream_t own_stream = nullptr;  // created for multi-group calls
+  cudaStream_t own_stream = nullptr;  // created for multi-group calls and default-stream callers
+  cudaEvent_t fork_ev = nullptr;      // orders own_stream after a default-stream caller
   int prof_on = 0;
   std::vector<cudaEvent_t> prof_ev;
   long long prof_rounds = 0;
@@ -178,6 +185,8 @@ pc_status propagate_with_tape(pc_plan *p, long long n_ic, const double *x0, doub
 __host__ __device__ inline int tape_rec(int n) { return 2 + 6 * n; }
 // pc_sweep.cu
 cudaError_t launch_init(const pc_plan *plan, const Sweep &s, const double *x0, cudaStream_t st);
+// Function attributes the round's kernels need (set outside any stream capture).
+cudaError_t prepare_launches(const pc_plan *plan);
 cudaError_t launch_round(const pc_plan *plan, const Sweep &s, int cur, cudaStream_t st,
                          cudaEvent_t *ev /* 5 events or nullptr */);
 // Moves the active slots of [0, s.A) to the front of the spare buffers (Y[cur]

@@ -294,6 +294,7 @@ void pcx::free_workspace(pc_plan *p) {
   if (w.h_cnt64) cudaFreeHost(w.h_cnt64);
   for (int i = 0; i < 2; i++)
     if (w.ev[i]) cudaEventDestroy(w.ev[i]);
+  if (w.graph) cudaGraphExecDestroy(w.graph);
   w = Workspace();
 }
 
@@ -303,6 +304,7 @@ extern "C" void pc_plan_destroy(pc_plan *p) {
   free_adjoint_workspace(p);
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   if (p->own_stream) cudaStreamDestroy(p->own_stream);
+  if (p->fork_ev) cudaEventDestroy(p->fork_ev);
   cudaFree(p->d_K);
   cudaFree(p->d_KTp);
   cudaFree(p->d_K32T);

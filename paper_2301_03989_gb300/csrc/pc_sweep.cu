@@ -1060,6 +1060,8 @@ Mix live_mix(const pc_plan *p) {
 // The FP32 operator goes to shared memory when it fits beside the force tables.
 constexpr size_t kFp32KsmemLimit = 120 * 1024;
 
+unsigned sm_ctas(const pc_plan *p, int per_sm) { return (unsigned)((p->num_sms > 0 ? p->num_sms : 152) * per_sm); }
+
 template <int NPL>
 void launch_fp32(const pc_plan *p, const Sweep &s, double *Y, const Mix &mx, cudaStream_t st) {
   const int n4 = (p->n + 3) & ~3;
@@ -1068,18 +1070,45 @@ void launch_fp32(const pc_plan *p, const Sweep &s, double *Y, const Mix &mx, cud
   const size_t g_bytes = (size_t)kFp32Warps * n4 * 6 * sizeof(float);
   const Ctl &c = p->ws.ctl[p->ws.live];
   if (k_bytes + g_bytes <= kFp32KsmemLimit) {
-    cudaFuncSetAttribute(k_fp32<NPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(k_bytes + g_bytes));
-    k_fp32<NPL, true><<<152 * 2, 32 * kFp32Warps, k_bytes + g_bytes, st>>>(s, c, p->model, p->d_K32T, p->d_mu32, Y,
-                                                                          mx);
+    k_fp32<NPL, true><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), 32 * kFp32Warps, k_bytes + g_bytes, st>>>(
+        s, c, p->model, p->d_K32T, p->d_mu32, Y, mx);
   } else {
-    cudaFuncSetAttribute(k_fp32<NPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_bytes);
-    k_fp32<NPL, false><<<152 * 2, 32 * kFp32Warps, g_bytes, st>>>(s, c, p->model, p->d_K32T, p->d_mu32, Y, mx);
+    k_fp32<NPL, false><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), 32 * kFp32Warps, g_bytes, st>>>(
+        s, c, p->model, p->d_K32T, p->d_mu32, Y, mx);
   }
+}
+
+// Shared-memory opt-in of the FP32 warp kernel for this plan's degree.
+template <int NPL>
+cudaError_t prepare_fp32(const pc_plan *p) {
+  const int n4 = (p->n + 3) & ~3;
+  const int lstride = ((NPL * n4 + 31) & ~31) + 4;
+  const size_t k_bytes = (size_t)32 * lstride * sizeof(float);
+  const size_t g_bytes = (size_t)kFp32Warps * n4 * 6 * sizeof(float);
+  if (k_bytes + g_bytes <= kFp32KsmemLimit)
+    return cudaFuncSetAttribute(k_fp32<NPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(k_bytes + g_bytes));
+  return cudaFuncSetAttribute(k_fp32<NPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_bytes);
 }
 
 }  // namespace
 
 // ---- launchers ----------------------------------------------------------------
+cudaError_t prepare_launches(const pc_plan *p) {
+  if (!p->npl) return cudaSuccess;
+  switch (p->npl) {
+    case 1: return prepare_fp32<1>(p);
+    case 2: return prepare_fp32<2>(p);
+    case 3: return prepare_fp32<3>(p);
+    case 4: return prepare_fp32<4>(p);
+    case 5: return prepare_fp32<5>(p);
+    case 6: return prepare_fp32<6>(p);
+    case 7: return prepare_fp32<7>(p);
+    case 8: return prepare_fp32<8>(p);
+    default: return prepare_fp32<9>(p);
+  }
+}
+
 cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cudaStream_t st) {
   const Workspace &w = p->ws;
   cudaError_t e = cudaMemsetAsync(w.ints, 0, 16 * sizeof(int), st);
@@ -1098,7 +1127,7 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   double *E = w.E[w.live], *Ai = w.Aind[w.live];
   const Mix mx = live_mix(p);
   if (ev) cudaEventRecord(ev[0], st);
-  k_setup<<<152 * 4, kThreads, 0, st>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
+  k_setup<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, st>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
   if (ev) cudaEventRecord(ev[1], st);
   if (s.mixed) {
     switch (p->npl) {
@@ -1117,9 +1146,9 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   k_force<<<dim3(blocks_for(s.A, 32), (s.n + kForceNodes - 1) / kForceNodes), dim3(32, kForceNodes), 0, st>>>(
       s, c, p->model, Yc, E, Ai, w.G, p->d_tau, w.tails);
   if (ev) cudaEventRecord(ev[3], st);
-  // persistent FP64 contraction: 4 CTAs of kSplit warps per SM
+  // persistent FP64 contraction: contract_ctas_per_sm CTAs of kSplit warps per SM
   const long long tiles = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
-  const long long blocks = std::min<long long>(152 * 4, tiles);
+  const long long blocks = std::max<long long>(1, std::min<long long>(sm_ctas(p, p->tune.contract_ctas_per_sm), tiles));
   k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn);
   if (ev) cudaEventRecord(ev[4], st);
   // one warp per block: the control work (resolution tests) spreads over all SMs

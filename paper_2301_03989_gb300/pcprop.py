@@ -25,7 +25,8 @@ PC_PREC_FP64, PC_PREC_MIXED = 0, 1
 EXPORTS = ["pc_options_default", "pc_plan_create", "pc_propagate", "pc_propagate_ex", "pc_eval_ephemeris",
            "pc_eval_dynamics", "pc_eval_warm_start", "pc_apply_operator", "pc_plan_operator", "pc_plan_destroy",
            "pc_status_string", "pc_plan_set_profiling", "pc_plan_kernel_times", "pc_apply_operator_static",
-           "pc_propagate_groups", "pc_propagate_tape", "pc_adjoint_tape", "pc_propagate_adjoint", "pc_bplane"]
+           "pc_propagate_groups", "pc_propagate_tape", "pc_adjoint_tape", "pc_propagate_adjoint", "pc_bplane",
+           "pc_plan_get_tuning", "pc_plan_set_tuning", "pc_plan_autotune"]
 KERNEL_NAMES = ["setup", "fp32", "force", "contract", "control"]
 
 
@@ -48,6 +49,14 @@ class Ephemeris(C.Structure):
 class KernelTimes(C.Structure):
     _fields_ = [("launches", C.c_longlong * 5), ("ms", C.c_double * 5), ("sweeps64", C.c_longlong),
                 ("sweeps32", C.c_longlong), ("kernel_launches", C.c_longlong)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("setup_ctas_per_sm", C.c_int), ("fp32_ctas_per_sm", C.c_int), ("contract_ctas_per_sm", C.c_int),
+                ("rounds_per_batch", C.c_int), ("repack_div", C.c_int), ("graphs", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class Options(C.Structure):
@@ -82,6 +91,9 @@ def lib():
             L.pc_adjoint_tape.argtypes = [vp, ll, vp, i, vp, vp, d, vp, vp, vp, vp]
             L.pc_propagate_adjoint.argtypes = [vp, ll, vp, d, d, d, vp, vp, vp]
             L.pc_bplane.argtypes = [vp, i, d, ll, vp, vp, vp, vp, vp, vp, vp]
+            L.pc_plan_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+            L.pc_plan_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+            L.pc_plan_autotune.argtypes = [vp, ll, vp, d, d, i, C.POINTER(Tuning), vp]
             L.pc_plan_operator.argtypes = [vp, vp, vp]
             L.pc_plan_destroy.argtypes = [vp]
             L.pc_plan_destroy.restype = None
@@ -258,6 +270,33 @@ def bplane(plan: Plan, body: int, mu_body: float, t, x, out=None, jac=None, out_
                            _ptr(out_bar), _ptr(x_bar), _stream(stream))
     _check(code, "pc_bplane", ok=(PC_OK, PC_ENONFINITE))
     return code
+
+
+def get_tuning(plan: Plan) -> dict:
+    t = Tuning()
+    _check(lib().pc_plan_get_tuning(plan.handle, C.byref(t)), "pc_plan_get_tuning")
+    return t.as_dict()
+
+
+def set_tuning(plan: Plan, **fields) -> dict:
+    """Changes the named launch-tuning fields (see pc.h); returns the new tuning."""
+    t = Tuning()
+    _check(lib().pc_plan_get_tuning(plan.handle, C.byref(t)), "pc_plan_get_tuning")
+    for k, v in fields.items():
+        if not hasattr(t, k):
+            raise AttributeError(k)
+        setattr(t, k, int(v))
+    _check(lib().pc_plan_set_tuning(plan.handle, C.byref(t)), "pc_plan_set_tuning")
+    return t.as_dict()
+
+
+def autotune(plan: Plan, x0, t0: float, tf: float, max_rounds: int = 200, stream=None) -> dict:
+    """Project autotuner (pc_plan_autotune): picks the plan's launch tuning by
+    timing capped propagations of x0 (planar [6][n_ic]); returns the choice."""
+    t = Tuning()
+    _check(lib().pc_plan_autotune(plan.handle, int(x0.shape[-1]), _ptr(x0), float(t0), float(tf), int(max_rounds),
+                                  C.byref(t), _stream(stream)), "pc_plan_autotune")
+    return t.as_dict()
 
 
 def eval_ephemeris(plan: Plan, t, rb, stream=None):

@@ -1,0 +1,88 @@
+"""Launch tuning, CUDA-graph replay and the autotuner: none of them may change
+a single bit of the results (they move work between CTAs, batch the host's
+round loop, or replay the same launches from a graph)."""
+import numpy as np
+import pytest
+
+from paper_2301_03989_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    import torch
+    from paper_2301_03989_gb300 import build, pcprop
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return pcprop
+
+
+def _run(pc, plan, w, x0d, tf, stream=None):
+    import torch
+    M = x0d.shape[1]
+    xf = torch.zeros_like(x0d)
+    st = torch.zeros(M, dtype=torch.int32, device="cuda")
+    it = torch.zeros(M, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(M, dtype=torch.int32, device="cuda")
+    code, rounds = pc.propagate(plan, x0d, w.t0, tf, xf, status=st, iters=it, nseg=ns, stream=stream)
+    torch.cuda.synchronize()
+    return code, rounds, xf.clone(), st.clone(), it.clone(), ns.clone()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tunings_and_graphs_are_bitwise_neutral(pc, precision):
+    import torch
+    w = W.config2(M=384)
+    prec = pc.PC_PREC_MIXED if precision == "mixed" else pc.PC_PREC_FP64
+    plan = pc.plan_from_workload(w, precision=prec)
+    x0d = torch.as_tensor(W.to_planar(w.x0), device="cuda")
+    tf = 0.25 * W.YEAR
+    base = _run(pc, plan, w, x0d, tf)
+    assert base[0] in (pc.PC_OK, pc.PC_ENOTCONV)
+    settings = [dict(graphs=0), dict(graphs=1, rounds_per_batch=2), dict(contract_ctas_per_sm=1, setup_ctas_per_sm=1),
+                dict(contract_ctas_per_sm=8, fp32_ctas_per_sm=4, setup_ctas_per_sm=16),
+                dict(repack_div=2, rounds_per_batch=16), dict(repack_div=64, rounds_per_batch=5, graphs=1)]
+    for kw in settings:
+        pc.set_tuning(plan, **kw)
+        r = _run(pc, plan, w, x0d, tf)
+        for a, b in zip(base[2:], r[2:]):
+            assert torch.equal(a, b), kw
+        pc.set_tuning(plan, setup_ctas_per_sm=4, fp32_ctas_per_sm=2, contract_ctas_per_sm=4, rounds_per_batch=8,
+                      repack_div=8, graphs=1)
+    # the caller's own (non-default) stream: no fork, graph captured on it directly
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        r = _run(pc, plan, w, x0d, tf, stream=s)
+    for a, b in zip(base[2:], r[2:]):
+        assert torch.equal(a, b)
+    plan.close()
+
+
+def test_tuning_validation(pc):
+    w = W.config1(M=8)
+    plan = pc.plan_from_workload(w)
+    for bad in (dict(setup_ctas_per_sm=0), dict(contract_ctas_per_sm=17), dict(rounds_per_batch=0),
+                dict(repack_div=1), dict(graphs=2), dict(fp32_ctas_per_sm=9)):
+        with pytest.raises(pc.PCError):
+            pc.set_tuning(plan, **bad)
+    assert pc.get_tuning(plan) == dict(setup_ctas_per_sm=4, fp32_ctas_per_sm=2, contract_ctas_per_sm=4,
+                                       rounds_per_batch=8, repack_div=8, graphs=1)
+    plan.close()
+
+
+def test_autotune_picks_a_neutral_setting(pc):
+    import torch
+    w = W.config2(M=512)
+    plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED)
+    x0d = torch.as_tensor(W.to_planar(w.x0), device="cuda")
+    tf = 0.25 * W.YEAR
+    pc.set_tuning(plan, graphs=0)
+    base = _run(pc, plan, w, x0d, tf)
+    best = pc.autotune(plan, x0d, w.t0, tf, max_rounds=64)
+    assert pc.get_tuning(plan) == best
+    r = _run(pc, plan, w, x0d, tf)
+    for a, b in zip(base[2:], r[2:]):
+        assert torch.equal(a, b)
+    print("autotuned:", best)
+    plan.close()
