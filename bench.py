@@ -202,9 +202,32 @@ def contract_flops_per_sweep(N: int) -> float:
     return 2.0 * N * (N + 1) * 6
 
 
+def timed_plain(pc, plan, w, x0, xf, st, it, stream, flush, steps, dev):
+    """The timed region: `steps` propagations (L2 flushed before each), CUDA
+    events on the launch stream around each, no per-kernel instrumentation.
+    Returns per-step ms, rounds and the kernel launches counted by the library."""
+    import torch
+    pc.kernel_times(plan)                       # clear the counters
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    rounds = 0
+    torch.cuda.synchronize(dev)
+    for k in range(steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        _, r = pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, iters=it, stream=stream)
+        rounds += r
+        ev1[k].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    kt = pc.kernel_times(plan)
+    return ms, rounds, kt
+
+
 def timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, steps, dev):
-    """Runs `steps` propagations (L2 flushed before each), CUDA events on the
-    launch stream around each; returns per-step ms, rounds and kernel times."""
+    """Instrumented replay of the timed steps: a CUDA event on the launch stream
+    between consecutive kernels of every round (direct launches), summed per
+    kernel.  Returns per-step ms, rounds and kernel times."""
     import torch
     pc.set_profiling(plan, True)
     pc.kernel_times(plan)                       # clear
@@ -244,7 +267,7 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     B.build()
-    wall = W.config2(M=IC_PER_RANK * world)
+    wall = W.config2(M=args.n_ic * world, years=args.years)
     lo, hi = shard(wall.n_ic, world, rank)
     w = wall.subset(np.arange(lo, hi))
     M = w.n_ic
@@ -259,6 +282,9 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
 
     with torch.cuda.stream(stream):
+        tuning = pc.get_tuning(plan)
+        if args.autotune:
+            tuning = pc.autotune(plan, x0, w.t0, w.tf, max_rounds=256, stream=stream)
         for _ in range(args.warmup):
             pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, iters=it, stream=stream)
         torch.cuda.synchronize(dev)
@@ -266,12 +292,14 @@ def run_ours(args, world, rank, local):
             torch.distributed.barrier()
         clocks = ClockSampler(local)
         clocks.start()
-        step_ms, rounds_total, ktimes = timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, args.steps, dev)
+        step_ms, rounds_total, kt_plain = timed_plain(pc, plan, w, x0, xf, st, it, stream, flush, args.steps, dev)
         if world > 1:
             torch.distributed.barrier()
         clk = clocks.stop()
         xf_main = xf.clone()
         status = st.cpu().numpy()
+        # per-kernel times: the same steps again with an event between kernels
+        prof_ms, _, ktimes = timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, args.steps, dev)
 
         # end to end through the C ABI with host buffers
         hx0 = torch.as_tensor(W.to_planar(w.x0)).pin_memory()
@@ -331,7 +359,9 @@ def run_ours(args, world, rank, local):
             "launches": launches_c, "avg_launch_us": 1000.0 * ms_c / max(1, launches_c),
             "algorithmic_flops_per_launch": flops / max(1, launches_c),
             "kernel_share": {k: ktimes[k][1] / max(1e-9, tsum) for k in names},
-            "dominant_by_time": kname}
+            "dominant_by_time": kname,
+            "timing": "CUDA events between consecutive kernels on the launch stream, over an instrumented "
+                      "replay of the timed steps (direct launches)"}
 
     line = None
     if rank == 0:
@@ -340,13 +370,14 @@ def run_ours(args, world, rank, local):
         if world == 1 and not args.no_cpu_baseline:
             rate, secs = oracle_rate(w, min(M, args.cpu_sample), cores)
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"first {min(M, args.cpu_sample)} trajectories of the workload, full 4-year arcs, "
-                             f"{secs:.1f} s on {cores} threads"}
+                   "sample": f"first {min(M, args.cpu_sample)} trajectories of the workload, full "
+                             f"{args.years:g}-year arcs, {secs:.1f} s on {cores} threads"}
         stats = {"sweep_rounds_per_step": rounds_total / max(1, args.steps),
                  "trajectory_sweeps_fp64_per_step": sweeps64 / max(1, args.steps),
                  "trajectory_sweeps_fp32_per_step": ktimes["sweeps32"] / max(1, args.steps),
                  "status_nonzero": int((status != 0).sum()),
-                 "kernel_ms_per_step": {k: ktimes[k][1] / args.steps for k in names}}
+                 "kernel_ms_per_step": {k: ktimes[k][1] / args.steps for k in names},
+                 "instrumented_ms_per_step": sum(prof_ms) / len(prof_ms)}
         if plain is not None:
             stats["plain_fp64"] = {
                 "value": total_ic / (plain["ms"] / 1000.0), "unit": UNIT, "ms_per_step": plain["ms"],
@@ -361,14 +392,15 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_ic_per_gpu": M, "N": w.N, "arc_years": 4, "tol": w.tol,
+            "config": {"workload": w.name, "n_ic_per_gpu": M, "N": w.N, "arc_years": args.years, "tol": w.tol,
                        "path": ("mixed FP32->FP64 batched sweep" if mixed else "plain FP64 batched sweep")
                                + " (per-trajectory segments, compaction, DMMA contraction)",
                        "switch_tol": args.switch_tol if mixed else None,
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}"},
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}",
+                       "tuning": tuning},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx0.numel() * 8),
                     "d2h_bytes_per_step": int(hxf.numel() * 8 + hst.numel() * 4)},
-            "gpu_launches": int(ktimes["kernel_launches"]),
+            "gpu_launches": int(kt_plain["kernel_launches"]),
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -378,6 +410,199 @@ def run_ours(args, world, rank, local):
     plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+# ----------------------------------------------------------------------------- other workloads
+def _oracle_reference(ora, w, x0, idx, N=None, S=None, t0=None, tf=None):
+    """Oracle final states (rows [len(idx)][6]) of the trajectories idx, on all
+    host cores (one trajectory per call when each has its own arc and degree)."""
+    from concurrent.futures import ThreadPoolExecutor
+    m = ora.Model.from_workload(w)
+    threads = os.cpu_count() or 1
+    if N is None:
+        o = ora.Opts(N=w.N, segments=w.segments, seg_mode=w.seg_mode, tol=w.tol, max_iters=w.max_iters,
+                     max_depth=w.max_depth)
+        return ora.propagate(m, o, x0[idx], w.t0, w.tf, threads=threads)["xf"]
+
+    def one(i):
+        o = ora.Opts(N=int(N[i]), segments=int(S[i]), seg_mode=0, tol=w.tol, max_iters=w.max_iters,
+                     max_depth=w.max_depth)
+        return ora.propagate(m, o, x0[i:i + 1], float(t0[i]), float(tf[i]))["xf"][0]
+    with ThreadPoolExecutor(threads) as ex:
+        return np.array(list(ex.map(one, idx)))
+
+
+def _errors(g, ref):
+    er = np.linalg.norm(g[:, :3] - ref[:, :3], axis=1) / np.linalg.norm(ref[:, :3], axis=1)
+    ev = np.linalg.norm(g[:, 3:] - ref[:, 3:], axis=1) / np.linalg.norm(ref[:, 3:], axis=1)
+    return {"n": int(len(ref)), "pos_max": float(er.max()), "pos_median": float(np.median(er)),
+            "vel_max": float(ev.max()), "vel_median": float(np.median(ev)),
+            "frac_within_1e-10": float(np.mean((er <= 1e-10) & (ev <= 1e-10)))}
+
+
+def _time_calls(fn, steps, warmup, stream, flush, dev):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def run_aux(args, world, rank, local):
+    """--workload precision | uneven | adjoint (1 GPU): the precision study
+    (65,536 config-1 trajectories, 2-year arcs, FP32 sweeps to 1e-6 then FP64 to
+    1e-13), uneven batching (up to 1,048,576 trajectories of mixed arc length,
+    degree and segment count, mixed precision, degree groups on concurrent
+    streams) and reverse mode (config-4 flybys: forward pass with tape plus one
+    reverse sweep).  Each prints one JSON line with its own metric."""
+    import torch
+    from paper_2301_03989_gb300 import build as B
+    from paper_2301_03989_gb300 import pcprop as pc
+    from paper_2301_03989_gb300 import workloads as W
+    if world > 1:
+        raise SystemExit("the extra workloads run on one GPU")
+    from oracle import oracle as ora
+    ora.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(0)
+    stats, config = {}, {}
+    clocks = ClockSampler(local)
+    with torch.cuda.stream(stream):
+        if args.workload == "precision":
+            w = W.config3(M=args.n_ic or 65536)
+            M = w.n_ic
+            x0 = torch.as_tensor(W.to_planar(w.x0), device=dev)
+            out = {}
+            for name, prec, sw in (("mixed", pc.PC_PREC_MIXED, 1e-6), ("fp64", pc.PC_PREC_FP64, 0.0)):
+                plan = pc.plan_from_workload(w, precision=prec, switch_tol=sw)
+                xf = torch.zeros_like(x0)
+                st = torch.zeros(M, dtype=torch.int32, device=dev)
+                if name == "mixed":
+                    clocks.start()
+                ms = _time_calls(lambda: pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, stream=stream),
+                                 args.steps, args.warmup, stream, flush, dev)
+                if name == "mixed":
+                    clk = clocks.stop()
+                kt = pc.kernel_times(plan)
+                out[name] = dict(ms=float(np.mean(ms)), xf=W.from_planar(xf.cpu().numpy()),
+                                 status=int((st.cpu().numpy() != 0).sum()), launches=int(kt["kernel_launches"]),
+                                 sweeps64=kt["sweeps64"], sweeps32=kt["sweeps32"])
+                plan.close()
+            idx = np.sort(rng.choice(M, size=min(M, args.oracle_sample), replace=False))
+            t = time.perf_counter()
+            ref = _oracle_reference(ora, w, w.x0, idx)
+            stats["error_vs_oracle_mixed"] = _errors(out["mixed"]["xf"][idx], ref)
+            stats["error_vs_oracle_fp64"] = _errors(out["fp64"]["xf"][idx], ref)
+            osecs = time.perf_counter() - t
+            ms = out["mixed"]["ms"]
+            n_steps = args.steps + args.warmup
+            stats["plain_fp64"] = {"value": M / (out["fp64"]["ms"] / 1000.0), "ms_per_step": out["fp64"]["ms"],
+                                   "speedup_mixed_over_plain": out["fp64"]["ms"] / ms,
+                                   "trajectory_sweeps_fp64_per_step": out["fp64"]["sweeps64"] / n_steps}
+            stats["mixed_sweeps_per_step"] = {"fp64": out["mixed"]["sweeps64"] / n_steps,
+                                              "fp32": out["mixed"]["sweeps32"] / n_steps}
+            stats["status_nonzero"] = out["mixed"]["status"]
+            launches = out["mixed"]["launches"] // n_steps * args.steps
+            metric = "trajectories/s (config-1 system, 2-year arcs, N=128): mixed FP32->FP64 vs plain FP64 GPU"
+            config = {"workload": w.name, "n_ic": M, "N": w.N, "switch_tol": 1e-6, "tol": w.tol,
+                      "oracle_sample": f"{len(idx)} seeded trajectories, oracle {osecs:.1f} s on {cores} threads"}
+        elif args.workload == "uneven":
+            uw = W.config5(M=args.n_ic or 1048576)
+            M = uw.n_ic
+            perm, degs, counts = uw.groups()
+            plans = []
+            b = uw.base
+            for d in degs:
+                o = pc.options_default(tol=b.tol, max_iters=b.max_iters, max_depth=b.max_depth, seg_mode=0,
+                                       precision=pc.PC_PREC_MIXED)
+                plans.append(pc.plan_create(int(d), 4, b.mu_central, b.mu, b.t_begin, b.granule, b.coef,
+                                            b.indirect, o))
+            x0 = torch.as_tensor(W.to_planar(uw.x0[perm]), device=dev)
+            t0 = torch.as_tensor(uw.t0[perm], device=dev)
+            tf = torch.as_tensor(uw.tf[perm], device=dev)
+            sg = torch.as_tensor(uw.S[perm].astype(np.int32), device=dev)
+            xf = torch.zeros_like(x0)
+            st = torch.zeros(M, dtype=torch.int32, device=dev)
+            for p_ in plans:
+                pc.kernel_times(p_)
+            clocks.start()
+            ms = _time_calls(lambda: pc.propagate_groups(plans, counts, x0, t0, tf, xf, segments=sg, status=st,
+                                                         stream=stream), args.steps, args.warmup, stream, flush, dev)
+            clk = clocks.stop()
+            n_steps = args.steps + args.warmup
+            launches = sum(pc.kernel_times(p_)["kernel_launches"] for p_ in plans) // n_steps * args.steps
+            xg = np.empty((M, 6))
+            xg[perm] = W.from_planar(xf.cpu().numpy())
+            stats["status_nonzero"] = int((st.cpu().numpy() != 0).sum())
+            idx = np.sort(rng.choice(M, size=min(M, max(8, args.oracle_sample // 16)), replace=False))
+            t = time.perf_counter()
+            ref = _oracle_reference(ora, b, uw.x0, idx, N=uw.N, S=uw.S, t0=uw.t0, tf=uw.tf)
+            stats["error_vs_oracle"] = _errors(xg[idx], ref)
+            osecs = time.perf_counter() - t
+            stats["groups"] = {int(d): int(c) for d, c in zip(degs, counts)}
+            for p_ in plans:
+                p_.close()
+            ms = float(np.mean(ms))
+            metric = "trajectories/s (uneven arcs 0.5-10 yr, N in {32,64,128,256}, 4-80 segments): mixed precision"
+            config = {"workload": uw.name, "n_ic": M, "degrees": [int(d) for d in degs],
+                      "oracle_sample": f"{len(idx)} seeded trajectories, oracle {osecs:.1f} s on {cores} threads"}
+        else:  # adjoint
+            w = W.config4(M=args.n_ic or 1024)
+            M = w.n_ic
+            plan = pc.plan_from_workload(w)
+            x0 = torch.as_tensor(W.to_planar(w.x0), device=dev)
+            cap = 256
+            rec = pc.tape_record(plan)
+            tape = torch.zeros(M * cap * rec, dtype=torch.float64, device=dev)
+            t0 = torch.full((M,), w.t0, dtype=torch.float64, device=dev)
+            tf = torch.full((M,), w.tf, dtype=torch.float64, device=dev)
+            xf = torch.zeros_like(x0)
+            ns = torch.zeros(M, dtype=torch.int32, device=dev)
+            xb = torch.as_tensor(rng.standard_normal((6, M)), device=dev)
+            x0b = torch.zeros_like(xb)
+
+            def fwd():
+                pc.propagate_tape(plan, x0, t0, tf, xf, ns, tape, cap, stream=stream)
+
+            def both():
+                fwd()
+                pc.adjoint_tape(plan, ns, cap, tape, xb, x0b, stream=stream)
+            pc.kernel_times(plan)
+            clocks.start()
+            ms = _time_calls(both, args.steps, args.warmup, stream, flush, dev)
+            clk = clocks.stop()
+            launches = pc.kernel_times(plan)["kernel_launches"] // (args.steps + args.warmup) * args.steps
+            ms_f = _time_calls(fwd, args.steps, 1, stream, flush, dev)
+            ms = float(np.mean(ms))
+            stats["forward_with_tape_ms"] = float(np.mean(ms_f))
+            stats["reverse_sweep_ms"] = ms - float(np.mean(ms_f))
+            stats["segments_max"] = int(ns.max().item())
+            plan.close()
+            metric = "trajectory gradients/s (config-4 Venus flybys, 1 revolution, N=128): forward tape + reverse sweep"
+            config = {"workload": w.name, "n_ic": M, "N": w.N, "tape_segments": cap}
+    ms_step = ms if isinstance(ms, float) else float(np.mean(ms))
+    line = {"metric": metric, "value": M / (ms_step / 1000.0), "unit": UNIT if args.workload != "adjoint"
+            else "trajectory gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": config, "gpu_launches": int(launches),
+            "clocks": clk, "stats": stats}
+    print(json.dumps(line))
     return 0
 
 
@@ -395,10 +620,20 @@ def main(argv=None):
                     help="FP32 -> FP64 switch threshold (0: when the FP32 change stops falling)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--workload", choices=["flyby", "precision", "uneven", "adjoint"], default="flyby",
+                    help="flyby: the headline workload; the others print their own line")
+    ap.add_argument("--n-ic", type=int, default=None, help="trajectories (per GPU for flyby)")
+    ap.add_argument("--years", type=float, default=4.0, help="arc length of the flyby workload")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--oracle-sample", type=int, default=512)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload != "flyby":
+        return run_aux(args, world, rank, local)
+    if args.n_ic is None:
+        args.n_ic = IC_PER_RANK
     return run_ours(args, world, rank, local)
 
 
