@@ -17,7 +17,8 @@
  * Parity status per function (what pins each one, see tests/test_oracle_*.py):
  *   ora_cgl_nodes        pinned: closed form, symmetry, endpoints
  *   ora_pc_operator      pinned: exact on polynomials, Clenshaw-Curtis weights
- *   ora_ephem_eval       pinned: numpy chebval, interpolation at fit nodes
+ *   ora_ephem_eval       pinned: numpy chebval, interpolation at fit nodes,
+ *                                 the later granule on a boundary
  *   ora_accel            pinned: finite-difference gradient of the potential,
  *                                collinear closed form, Kepler conservation
  *   ora_kepler           pinned: Kepler's-equation residual, energy/momentum,
@@ -178,11 +179,16 @@ void ora_pc_operator(int N, int truncated, double *K) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Ephemeris: Clenshaw evaluation of one body's granule.  The paper     */
+/* Ephemeris: the table's Chebyshev series written out,                 */
+/*   r_b = sum_{k=0}^{deg} c_k T_k(sigma),                               */
+/* with T_0 = 1, T_1 = sigma, T_{k+1} = 2 sigma T_k - T_{k-1}, and the   */
+/* sum taken from the highest degree down, one fused multiply-add (one  */
+/* rounding, C99 fma) per recurrence step and per term.  The paper      */
 /* evaluates planetary states once at the fixed node times before the   */
-/* iterations (Section "Dynamics model, array sorting, and CUDA kernel").*/
-/* A time exactly on a granule boundary uses the later granule; times   */
-/* outside the table use the nearest granule.                           */
+/* iterations (Section "Dynamics model, array sorting, and CUDA kernel")*/
+/* and does not fix how the tables are summed.  A time exactly on a     */
+/* granule boundary uses the later granule; times outside the table use */
+/* the nearest granule.  Degrees above 63 are not supported (zeros).    */
 /* ------------------------------------------------------------------ */
 void ora_ephem_eval(const ora_model *m, double t, double *rb /* [n_bodies][3] */) {
   const int nc = m->degree + 1;
@@ -191,16 +197,19 @@ void ora_ephem_eval(const ora_model *m, double t, double *rb /* [n_bodies][3] */
   if (g > m->n_granules - 1) g = m->n_granules - 1;
   const double tg = m->t_begin + (double)g * m->granule;
   const double sigma = 2.0 * (t - tg) / m->granule - 1.0;
+  double T[64];
+  for (int b = 0; b < m->n_bodies; b++)
+    for (int ax = 0; ax < 3; ax++) rb[b * 3 + ax] = 0.0;
+  if (nc > 64) return;
+  T[0] = 1.0;
+  if (nc > 1) T[1] = sigma;
+  for (int k = 2; k < nc; k++) T[k] = fma(2.0 * sigma, T[k - 1], -T[k - 2]);
   for (int b = 0; b < m->n_bodies; b++) {
     for (int ax = 0; ax < 3; ax++) {
       const double *c = m->coef + (((size_t)b * m->n_granules + g) * 3 + ax) * nc;
-      double b1 = 0.0, b2 = 0.0;
-      for (int k = nc - 1; k >= 1; k--) {
-        double b0 = c[k] + 2.0 * sigma * b1 - b2;
-        b2 = b1;
-        b1 = b0;
-      }
-      rb[b * 3 + ax] = c[0] + sigma * b1 - b2;
+      double acc = 0.0;
+      for (int k = nc - 1; k >= 0; k--) acc = fma(c[k], T[k], acc);
+      rb[b * 3 + ax] = acc;
     }
   }
 }
