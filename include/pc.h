@@ -71,7 +71,7 @@ typedef struct {
 /* Ephemeris: granule g covers [t_begin + g*granule_s, t_begin + (g+1)*granule_s)
  * (a time on a boundary uses the later granule; times outside the table use
  * the nearest granule); inside it sigma = 2 (t - t_g)/granule_s - 1 and
- * r_b(t) = sum_k coef[b][g][axis][k] T_k(sigma).  The paper evaluates the
+ * r_b(t) = sum_k coef[b][g][axis][k] T_k(sigma) (degree at most 63).  The paper evaluates the
  * planetary data once per set of node times, before the iterations (Section
  * "Dynamics model"); so does this library, once per segment. */
 typedef struct {
@@ -156,7 +156,8 @@ pc_status pc_propagate_ex(pc_plan *plan, long long n_ic, const double *x0, doubl
  * are asynchronous on `stream` and use the plan's workspace (same rule as
  * pc_propagate: one plan per concurrently used stream). */
 
-/* Ephemeris (Clenshaw) at n_pts times t [n_pts]: rb planar [n_bodies][3][n_pts]. */
+/* Ephemeris (the table's Chebyshev series) at n_pts times t [n_pts]: rb planar
+ * [n_bodies][3][n_pts]. */
 pc_status pc_eval_ephemeris(pc_plan *plan, long long n_pts, const double *t, double *rb, void *stream);
 
 /* Dynamics f(y, t) = (v, a(r, t)) of Eq. (ibvp) with the plan's force model at
@@ -238,7 +239,11 @@ pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
  *                         its slots have finished (2..64)
  *   graphs                1: each batch of rounds is captured once per working-set
  *                         shape as a CUDA graph and replayed (0: direct launches)
- * Defaults: 4, 2, 4, 8, 8, 1.  Profiling (pc_plan_set_profiling) launches
+ *   side_priority         mixed precision: 1 runs the new-segment branch of each
+ *                         round (set-up, FP32 phase) on a stream of the device's
+ *                         highest priority beside the FP64 branch, 0 at default
+ *                         priority
+ * Defaults: 4, 1, 4, 8, 8, 1, 1.  Profiling (pc_plan_set_profiling) launches
  * directly whatever `graphs` says. */
 typedef struct {
   int setup_ctas_per_sm;
@@ -247,6 +252,7 @@ typedef struct {
   int rounds_per_batch;
   int repack_div;
   int graphs;
+  int side_priority;
 } pc_tuning;
 
 /* Reads / replaces the plan's tuning (PC_EINVAL on a value out of range). */
@@ -254,7 +260,8 @@ pc_status pc_plan_get_tuning(const pc_plan *plan, pc_tuning *out);
 pc_status pc_plan_set_tuning(pc_plan *plan, const pc_tuning *t);
 
 /* Autotuner: coordinate descent over the tuning fields (contraction CTAs,
- * set-up CTAs, FP32 CTAs, rounds per batch, compaction threshold, graphs), each
+ * set-up CTAs, FP32 CTAs, side-branch priority, rounds per batch, compaction
+ * threshold, graphs), each
  * candidate timed with CUDA events on a propagation of the caller's
  * trajectories x0 (device, planar [6][n_ic]) over [t0, tf] capped at
  * max_rounds sweep rounds (>= 16).  The fastest setting per round is kept in

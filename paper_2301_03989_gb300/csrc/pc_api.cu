@@ -122,6 +122,21 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   S.finished = S.capped = false;
   p->session_id += 1;  // a new call: kernel arguments differ, no cached graph applies
   S.e = prepare_launches(p);
+  if (S.e == cudaSuccess && mixed && p->side_stream && p->side_stream_prio != p->tune.side_priority) {
+    S.e = cudaStreamSynchronize(p->side_stream);
+    cudaStreamDestroy(p->side_stream);
+    p->side_stream = nullptr;
+  }
+  if (S.e == cudaSuccess && mixed && !p->side_stream) {
+    int least = 0, greatest = 0;
+    S.e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (S.e == cudaSuccess)
+      S.e = cudaStreamCreateWithPriority(&p->side_stream, cudaStreamNonBlocking,
+                                         p->tune.side_priority ? greatest : 0);
+    p->side_stream_prio = p->tune.side_priority;
+  }
+  for (int k = 0; k < 2 && S.e == cudaSuccess && mixed; k++)
+    if (!p->branch_ev[k]) S.e = cudaEventCreateWithFlags(&p->branch_ev[k], cudaEventDisableTiming);
   if (S.e == cudaSuccess) S.e = launch_init(p, s, x0, st);
   return S.e == cudaSuccess ? PC_OK : cuda_status(S.e);
 }
@@ -452,7 +467,8 @@ extern "C" pc_status pc_plan_set_tuning(pc_plan *p, const pc_tuning *t) {
   if (!p || !t) return PC_EINVAL;
   if (t->setup_ctas_per_sm < 1 || t->setup_ctas_per_sm > 16 || t->fp32_ctas_per_sm < 1 || t->fp32_ctas_per_sm > 8 ||
       t->contract_ctas_per_sm < 1 || t->contract_ctas_per_sm > 16 || t->rounds_per_batch < 1 ||
-      t->rounds_per_batch > 64 || t->repack_div < 2 || t->repack_div > 64 || (t->graphs != 0 && t->graphs != 1))
+      t->rounds_per_batch > 64 || t->repack_div < 2 || t->repack_div > 64 || (t->graphs != 0 && t->graphs != 1) ||
+      (t->side_priority != 0 && t->side_priority != 1))
     return PC_EINVAL;
   p->tune = *t;
   return PC_OK;
@@ -497,9 +513,10 @@ extern "C" pc_status pc_plan_autotune(pc_plan *p, long long n_ic, const double *
     std::vector<int> values;
   };
   const std::vector<Axis> axes = {
-      {&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8}},
-      {&pc_tuning::setup_ctas_per_sm, {2, 4, 8}},
+      {&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8, 12, 16}},
+      {&pc_tuning::setup_ctas_per_sm, {1, 2, 4, 8}},
       {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{}},
+      {&pc_tuning::side_priority, mixed ? std::vector<int>{0, 1} : std::vector<int>{}},
       {&pc_tuning::rounds_per_batch, {4, 8, 16, 32}},
       {&pc_tuning::repack_div, {4, 8, 16}},
       {&pc_tuning::graphs, {0, 1}},

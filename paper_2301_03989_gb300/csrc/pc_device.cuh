@@ -27,11 +27,14 @@ __device__ __forceinline__ unsigned err_bits32(float e) {
 }
 
 // ---------------------------------------------------------------------------
-// Ephemeris: Clenshaw evaluation of body b at time t,
-//   b_k = c_k + 2 sigma b_{k+1} - b_{k+2},  r = c_0 + sigma b_1 - b_2.
-// Every operation is rounded on its own (no fused multiply-add), so the body
-// positions are the exactly rounded results of this recurrence: near a body
-// the force amplifies a position rounding difference by |r| / |r - r_b|.
+// Ephemeris: the table's Chebyshev series r = sum_k c_k T_k(sigma) at the
+// granule holding t.  T_0 = 1, T_1 = sigma, T_{k+1} = fma(2 sigma, T_k, -T_{k-1})
+// are formed once per time and shared by every body and axis; each coordinate
+// is then summed from the top degree down with one fused multiply-add per
+// term.  Every step is a single correctly rounded operation, so the body
+// positions are bitwise those of the CPU oracle's evaluation of the same
+// series.  Near a body the force amplifies a position rounding difference by
+// |r| / |r - r_b|, which is why the two must agree exactly.
 // ---------------------------------------------------------------------------
 struct EphemLoc {
   int g;
@@ -45,19 +48,56 @@ __device__ __forceinline__ EphemLoc ephem_locate(const Model &md, double t) {
   return {g, dsub(dmul(2.0, dsub(t, tg)) / md.granule, 1.0)};
 }
 
-__device__ __forceinline__ void ephem_body(const Model &md, EphemLoc L, int b, double r[3]) {
-  const double s2 = dmul(2.0, L.sig);
+constexpr int kEphemRegCoefs = 16;  // degrees up to 15 keep T_k in registers
+constexpr int kEphemMaxCoefs = 64;  // degrees up to 63
+
+// Calls out(b, r) for every body b in order with its position r[3].
+template <class Out>
+__device__ __forceinline__ void ephem_all(const Model &md, EphemLoc L, Out out) {
   const int nc = md.deg + 1;
-  for (int ax = 0; ax < 3; ax++) {
-    const double *cf = md.coef + (((size_t)b * md.n_gr + L.g) * 3 + ax) * nc;
-    double b1 = 0.0, b2 = 0.0;
-    for (int k = nc - 1; k >= 1; k--) {
-      const double b0 = dsub(dadd(cf[k], dmul(s2, b1)), b2);
-      b2 = b1;
-      b1 = b0;
+  const double s2 = 2.0 * L.sig;
+  if (nc <= kEphemRegCoefs) {
+    double T[kEphemRegCoefs];
+    T[0] = 1.0;
+    T[1] = L.sig;
+#pragma unroll
+    for (int k = 2; k < kEphemRegCoefs; k++) T[k] = fma(s2, T[k - 1], -T[k - 2]);
+    for (int b = 0; b < md.B; b++) {
+      const double *cf = md.coef + ((size_t)b * md.n_gr + L.g) * 3 * nc;
+      double r[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = kEphemRegCoefs - 1; k >= 0; k--)
+        if (k < nc)
+#pragma unroll
+          for (int ax = 0; ax < 3; ax++) r[ax] = fma(cf[ax * nc + k], T[k], r[ax]);
+      out(b, r);
     }
-    r[ax] = dsub(dadd(cf[0], dmul(L.sig, b1)), b2);
+  } else {
+    double T[kEphemMaxCoefs];
+    const int m = nc < kEphemMaxCoefs ? nc : kEphemMaxCoefs;
+    T[0] = 1.0;
+    T[1] = L.sig;
+    for (int k = 2; k < m; k++) T[k] = fma(s2, T[k - 1], -T[k - 2]);
+    for (int b = 0; b < md.B; b++) {
+      const double *cf = md.coef + ((size_t)b * md.n_gr + L.g) * 3 * nc;
+      double r[3] = {0.0, 0.0, 0.0};
+      for (int k = m - 1; k >= 0; k--)
+        for (int ax = 0; ax < 3; ax++) r[ax] = fma(cf[ax * nc + k], T[k], r[ax]);
+      out(b, r);
+    }
   }
+}
+
+// One body's position (same arithmetic as ephem_all).
+__device__ __forceinline__ void ephem_body(const Model &md, EphemLoc L, int body, double r[3]) {
+  Model one = md;
+  one.coef = md.coef + (size_t)body * md.n_gr * 3 * (md.deg + 1);
+  one.B = 1;
+  ephem_all(one, L, [&](int, const double p[3]) {
+    r[0] = p[0];
+    r[1] = p[1];
+    r[2] = p[2];
+  });
 }
 
 // FP64 tensor-core MMA, mma.sync m16n8k4 .f64 (PTX ISA).  Fragment layouts,

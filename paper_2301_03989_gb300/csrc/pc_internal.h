@@ -19,7 +19,9 @@ constexpr int kMaxNpl = 9;   // mixed precision: N + 1 <= 32 * kMaxNpl (N <= 287
 __host__ __device__ constexpr int x32_stride(int B) { return 12 + 4 * B; }
 
 // Trajectory phases: FP64 sweeps, finished, FP32 sweeps (mixed precision).
-enum : int { PH_ITER = 0, PH_DONE = 1, PH_ITER32 = 2 };
+// PH_READY64: the FP32 phase ended in this round's k_fp32; the control kernel
+// moves the trajectory to PH_ITER and onto the next round's FP64 list.
+enum : int { PH_ITER = 0, PH_DONE = 1, PH_ITER32 = 2, PH_READY64 = 3 };
 
 // Segment-attempt outcomes.
 enum : int { SEG_CONTINUE = -1, SEG_OK = 0, SEG_STALLED = 1, SEG_FAIL_CAP = 2, SEG_FAIL_DIV = 3, SEG_FAIL_TRUNC = 4 };
@@ -139,7 +141,7 @@ struct pc_plan {
   int N = 0, n = 0, kpad = 0, rows_pad = 0;
   int segments = 0;
   pc_options opt{};
-  pc_tuning tune{4, 2, 4, 8, 8, 1};
+  pc_tuning tune{4, 1, 4, 8, 8, 1, 1};
   long long session_id = 0;  // distinguishes calls for the graph cache
   int device = 0;
   // model (device copies)
@@ -165,6 +167,11 @@ struct pc_plan {
   // contract, the FP32 kernels, control, after control)
   cudaStream_t own_stream = nullptr;  // created for multi-group calls and default-stream callers
   cudaEvent_t fork_ev = nullptr;      // orders own_stream after a default-stream caller
+  // mixed precision: the new-segment branch of a round (set-up, FP32 phase) runs
+  // on side_stream beside the FP64 branch (force, contraction)
+  cudaStream_t side_stream = nullptr;
+  int side_stream_prio = -1;          // side_priority the side stream was created with
+  cudaEvent_t branch_ev[2] = {nullptr, nullptr};  // fork, join
   int prof_on = 0;
   std::vector<cudaEvent_t> prof_ev;
   long long prof_rounds = 0;

@@ -104,7 +104,7 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
   const int B = force->n_bodies;
   if (B < 0 || B > kMaxBodies || !(force->mu_central > 0.0) || (B > 0 && !force->mu)) return PC_EINVAL;
   if (B > 0) {
-    if (!ephem || ephem->n_bodies != B || !(ephem->granule_s > 0.0) || ephem->degree < 0 ||
+    if (!ephem || ephem->n_bodies != B || !(ephem->granule_s > 0.0) || ephem->degree < 0 || ephem->degree > 63 ||
         ephem->n_granules < 1 || !ephem->coef)
       return PC_EINVAL;
   }
@@ -305,6 +305,9 @@ extern "C" void pc_plan_destroy(pc_plan *p) {
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   if (p->own_stream) cudaStreamDestroy(p->own_stream);
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  if (p->side_stream) cudaStreamDestroy(p->side_stream);
+  for (int k = 0; k < 2; k++)
+    if (p->branch_ev[k]) cudaEventDestroy(p->branch_ev[k]);
   cudaFree(p->d_K);
   cudaFree(p->d_KTp);
   cudaFree(p->d_K32T);

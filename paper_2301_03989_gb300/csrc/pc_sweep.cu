@@ -229,15 +229,13 @@ struct Mix {
 // (grid-stride over list entries x nodes, entries fastest).  With mixed
 // precision the warm start goes to YK and the FP32 node records to X32 (both
 // by list entry) for k_fp32; otherwise the warm start is the first iterate.
-// Block 0 clears the lists this round's control kernel fills and the tile
-// counter.
+// Block 0 clears the lists this round's control kernel fills.
 __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau, double *__restrict__ Y,
                         double *__restrict__ E, double *__restrict__ Aind, Mix mx) {
   const int cur = s.list_cur;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     s.list_cnt[cur ^ 1] = 0;
     s.l64_cnt[cur ^ 1] = 0;
-    *s.tile_ctr = 0;
   }
   const long long count = s.list_cnt[cur];
   const int *__restrict__ list = s.list[cur];
@@ -258,16 +256,14 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     float *rec = s.mixed ? mx.X32 + ((size_t)e * s.n + j) * mx.xs : nullptr;
     const EphemLoc L = ephem_locate(md, t);
     double ind[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < B; b++) {
-      double r[3];
-      ephem_body(md, L, b, r);
+    ephem_all(md, L, [&](int b, const double r[3]) {
       for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
       if (md.indirect) add_indirect(md, b, r, ind);
       if (rec) {
         for (int ax = 0; ax < 3; ax++) rec[12 + 4 * b + ax] = (float)(y[ax] - r[ax]);
         rec[15 + 4 * b] = 0.0f;
       }
-    }
+    });
     for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
     if (rec) {
       double *yk = mx.YK + ((size_t)e * s.n + j) * 6;
@@ -570,14 +566,17 @@ __global__ void __launch_bounds__(32 * kSplit) k_contract_diag(Sweep s, Ctl c, c
 // block stages the FP32 operator K32T ([N+1][32 NPL], transposed) in shared
 // memory when KSMEM.  The sweeps stop when the change is below switch_tol or
 // the FP32 floor, fails to halve the best change for two sweeps, or reaches
-// max_iters: then Y = y_K + delta is written and the trajectory joins this
-// round's FP64 list.  A non-finite or huge change leaves the trajectory in the
-// FP32 phase with that change, and the control kernel halves the segment.
-constexpr int kFp32Warps = 8;
+// max_iters: then Y = y_K + delta is written to the next round's buffer and
+// the control kernel puts the trajectory on the next round's FP64 list.  A
+// non-finite or huge change leaves the trajectory in the FP32 phase with that
+// change, and the control kernel halves the segment.  Four warps per CTA keep
+// a CTA's registers (at most 128 per thread) and shared memory small enough to
+// sit beside the FP64 branch's CTAs, which run at the same time.
+constexpr int kFp32Warps = 4;
 constexpr float kFp32Floor = 2e-6f;
 
 template <int NPL, bool KSMEM>
-__global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model md, const float *__restrict__ K32T,
+__global__ void __launch_bounds__(32 * kFp32Warps, 4) k_fp32(Sweep s, Ctl c, Model md, const float *__restrict__ K32T,
                                                         const float *__restrict__ mu32, double *__restrict__ Y,
                                                         Mix mx) {
   extern __shared__ float4 fp32_smem4[];
@@ -775,12 +774,10 @@ __global__ void __launch_bounds__(32 * kFp32Warps) k_fp32(Sweep s, Ctl c, Model 
       if (fail) {
         c.err32[m] = err_bits32(efin);
       } else {
-        c.phase[m] = PH_ITER;
+        c.phase[m] = PH_READY64;
         c.seg_sweeps[m] = 0;
         c.nstall[m] = 0;
         c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);
-        const int k = atomicAdd(s.l64_cnt + cur, 1);
-        s.l64[cur][k] = m;
       }
     }
     __syncwarp();
@@ -837,9 +834,15 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
   const int lane = threadIdx.x & 31;
   const int phase = (m < s.A) ? c.phase[m] : PH_DONE;
   const bool act = phase == PH_ITER || phase == PH_ITER32;
+  const bool ready = phase == PH_READY64;  // FP32 phase done this round: FP64 sweeps from the next
   const int ld = s.ld;
   const int list_next = s.list_cur ^ 1;
   int out = SEG_CONTINUE;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s.tile_ctr = 0;  // this round's contraction is over
+  if (ready) {
+    c.need_setup[m] = 0;
+    c.phase[m] = PH_ITER;
+  }
   {
     const unsigned n64 = __popc(__ballot_sync(0xffffffffu, phase == PH_ITER));
     if (lane == 0 && n64) atomicAdd(s.cnt64, (unsigned long long)n64);
@@ -920,7 +923,7 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
       }
     }
   }
-  const bool next64 = act && c.phase[m] == PH_ITER;
+  const bool next64 = (act && c.phase[m] == PH_ITER) || ready;
   warp_append(next64, m, s.l64[list_next], s.l64_cnt + list_next);
 }
 
@@ -1007,11 +1010,9 @@ __global__ void k_eval_ephem(Model md, long long n, const double *__restrict__ t
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const EphemLoc L = ephem_locate(md, t[i]);
-  for (int b = 0; b < md.B; b++) {
-    double r[3];
-    ephem_body(md, L, b, r);
+  ephem_all(md, L, [&](int b, const double r[3]) {
     for (int ax = 0; ax < 3; ax++) rb[(size_t)(b * 3 + ax) * n + i] = r[ax];
-  }
+  });
 }
 
 __global__ void k_eval_warm(Model md, long long n, const double *__restrict__ x0, const double *__restrict__ dt,
@@ -1126,21 +1127,37 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   double *Yc = w.Y[cur], *Yn = w.Y[cur ^ 1];
   double *E = w.E[w.live], *Ai = w.Aind[w.live];
   const Mix mx = live_mix(p);
+  // Mixed precision without per-kernel events: the new-segment branch (set-up,
+  // FP32 phase; its trajectories join the FP64 list next round) and the FP64
+  // branch (force, contraction over this round's FP64 list) touch disjoint
+  // trajectories, so they run side by side and join before the control kernel.
+  const bool branches = s.mixed && !ev && p->side_stream;
+  cudaStream_t sb = branches ? p->side_stream : st;
+  cudaError_t e = cudaSuccess;
+  if (branches) {
+    e = cudaEventRecord(p->branch_ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sb, p->branch_ev[0], 0);
+    if (e != cudaSuccess) return e;
+  }
   if (ev) cudaEventRecord(ev[0], st);
-  k_setup<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, st>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
+  k_setup<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
   if (ev) cudaEventRecord(ev[1], st);
   if (s.mixed) {
     switch (p->npl) {
-      case 1: launch_fp32<1>(p, s, Yc, mx, st); break;
-      case 2: launch_fp32<2>(p, s, Yc, mx, st); break;
-      case 3: launch_fp32<3>(p, s, Yc, mx, st); break;
-      case 4: launch_fp32<4>(p, s, Yc, mx, st); break;
-      case 5: launch_fp32<5>(p, s, Yc, mx, st); break;
-      case 6: launch_fp32<6>(p, s, Yc, mx, st); break;
-      case 7: launch_fp32<7>(p, s, Yc, mx, st); break;
-      case 8: launch_fp32<8>(p, s, Yc, mx, st); break;
-      default: launch_fp32<9>(p, s, Yc, mx, st); break;
+      case 1: launch_fp32<1>(p, s, Yn, mx, sb); break;
+      case 2: launch_fp32<2>(p, s, Yn, mx, sb); break;
+      case 3: launch_fp32<3>(p, s, Yn, mx, sb); break;
+      case 4: launch_fp32<4>(p, s, Yn, mx, sb); break;
+      case 5: launch_fp32<5>(p, s, Yn, mx, sb); break;
+      case 6: launch_fp32<6>(p, s, Yn, mx, sb); break;
+      case 7: launch_fp32<7>(p, s, Yn, mx, sb); break;
+      case 8: launch_fp32<8>(p, s, Yn, mx, sb); break;
+      default: launch_fp32<9>(p, s, Yn, mx, sb); break;
     }
+  }
+  if (branches) {
+    e = cudaEventRecord(p->branch_ev[1], sb);
+    if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[2], st);
   k_force<<<dim3(blocks_for(s.A, 32), (s.n + kForceNodes - 1) / kForceNodes), dim3(32, kForceNodes), 0, st>>>(
@@ -1150,6 +1167,10 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   const long long tiles = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
   const long long blocks = std::max<long long>(1, std::min<long long>(sm_ctas(p, p->tune.contract_ctas_per_sm), tiles));
   k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn);
+  if (branches) {
+    e = cudaStreamWaitEvent(st, p->branch_ev[1], 0);
+    if (e != cudaSuccess) return e;
+  }
   if (ev) cudaEventRecord(ev[4], st);
   // one warp per block: the control work (resolution tests) spreads over all SMs
   k_control<<<blocks_for(s.A, 32), 32, 0, st>>>(s, c, w.tails, Yn, w.ints);
