@@ -86,7 +86,8 @@ typedef struct {
 #define PC_PREC_FP64 0   /* every sweep in FP64 */
 #define PC_PREC_MIXED 1  /* each segment first runs FP32 sweeps on the deviation from its warm start
                             until the change is below switch_tol or stops falling, then FP64 sweeps
-                            to tol (not in the paper: an extension); needs N <= 287 */
+                            to tol, with FP32 correction solves between them (refine32); not in
+                            the paper: an extension; needs N <= 287 */
 
 typedef struct {
   double tol;          /* stopping tolerance on the sweep-to-sweep change (overridden per call) */
@@ -104,11 +105,14 @@ typedef struct {
   double switch_tol;   /* mixed precision: FP32 sweeps until the change is below this (0: until the
                           FP32 change stops falling) */
   long long max_rounds;/* safety cap on sweep rounds per call (0 = 10,000,000) */
+  int refine32;        /* mixed precision: 1 lets an FP64 sweep whose change is below 1e-3 be
+                          followed by an FP32 solve for the correction to its iterate (up to
+                          two per segment attempt) instead of further FP64 sweeps */
 } pc_options;
 
 /* Fills *o with the defaults: tol 1e-13, relative 1, max_iters 60, max_depth 8,
  * warm_start 1, seg_mode 0, truncated 0, stall_sweeps 5, stall_factor 1e3,
- * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0.
+ * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0, refine32 1.
  * Returns PC_EINVAL if o is NULL. */
 pc_status pc_options_default(pc_options *o);
 
@@ -231,7 +235,7 @@ pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
  * Launch shapes of the sweep kernels and the host's round loop.  None of them
  * changes any arithmetic: results are bitwise the same for every setting.
  *   setup_ctas_per_sm     CTAs per SM of the new-segment set-up kernel (1..16)
- *   fp32_ctas_per_sm      CTAs per SM of the FP32 warp kernel (1..8)
+ *   fp32_ctas_per_sm      CTAs per SM of the FP32 kernels (1..16; one trajectory per CTA at a time)
  *   contract_ctas_per_sm  persistent CTAs per SM of the FP64 contraction (1..16)
  *   rounds_per_batch      sweep rounds queued between two looks at the device's
  *                         done counter (1..64)
@@ -243,7 +247,7 @@ pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
  *                         round (set-up, FP32 phase) on a stream of the device's
  *                         highest priority beside the FP64 branch, 0 at default
  *                         priority
- * Defaults: 4, 1, 4, 8, 8, 1, 1.  Profiling (pc_plan_set_profiling) launches
+ * Defaults: 4, 4, 4, 8, 8, 1, 1.  Profiling (pc_plan_set_profiling) launches
  * directly whatever `graphs` says. */
 typedef struct {
   int setup_ctas_per_sm;

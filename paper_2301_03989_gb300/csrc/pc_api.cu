@@ -85,12 +85,18 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   s.nseg = nseg;
   s.mixed = mixed;
   s.switch_tol = o.switch_tol;
+  s.refine = mixed && o.refine32;
+  s.max_corr = 2;
+  s.corr_hi = 1e-3;
   s.list[0] = w.lists;
   s.list[1] = w.lists + w.ld;
   s.list_cnt = w.ints + 2;
   s.l64[0] = w.lists + 2 * (size_t)w.ld;
   s.l64[1] = w.lists + 3 * (size_t)w.ld;
   s.l64_cnt = w.ints + 5;
+  s.lc[0] = w.lists + 4 * (size_t)w.ld;
+  s.lc[1] = w.lists + 5 * (size_t)w.ld;
+  s.lc_cnt = w.ints + 8;
   s.tile_ctr = w.ints + 7;
   s.cnt64 = w.cnt64;
   s.list_cur = 0;
@@ -465,7 +471,7 @@ extern "C" pc_status pc_plan_get_tuning(const pc_plan *p, pc_tuning *out) {
 
 extern "C" pc_status pc_plan_set_tuning(pc_plan *p, const pc_tuning *t) {
   if (!p || !t) return PC_EINVAL;
-  if (t->setup_ctas_per_sm < 1 || t->setup_ctas_per_sm > 16 || t->fp32_ctas_per_sm < 1 || t->fp32_ctas_per_sm > 8 ||
+  if (t->setup_ctas_per_sm < 1 || t->setup_ctas_per_sm > 16 || t->fp32_ctas_per_sm < 1 || t->fp32_ctas_per_sm > 16 ||
       t->contract_ctas_per_sm < 1 || t->contract_ctas_per_sm > 16 || t->rounds_per_batch < 1 ||
       t->rounds_per_batch > 64 || t->repack_div < 2 || t->repack_div > 64 || (t->graphs != 0 && t->graphs != 1) ||
       (t->side_priority != 0 && t->side_priority != 1))
@@ -515,7 +521,7 @@ extern "C" pc_status pc_plan_autotune(pc_plan *p, long long n_ic, const double *
   const std::vector<Axis> axes = {
       {&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8, 12, 16}},
       {&pc_tuning::setup_ctas_per_sm, {1, 2, 4, 8}},
-      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{}},
+      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{2, 4, 6, 8, 12} : std::vector<int>{}},
       {&pc_tuning::side_priority, mixed ? std::vector<int>{0, 1} : std::vector<int>{}},
       {&pc_tuning::rounds_per_batch, {4, 8, 16, 32}},
       {&pc_tuning::repack_div, {4, 8, 16}},

@@ -13,15 +13,20 @@ constexpr int kMaxBodies = 32;
 constexpr int kMaxN = 512;
 constexpr int kMaxNpl = 9;   // mixed precision: N + 1 <= 32 * kMaxNpl (N <= 287)
 
-// Floats per node in the FP32 record of a new segment (mixed precision):
-// float4 groups (r_K, mu_c/|r_K|^3), (v_K, -), (indirect term, -), then one
-// (r_K - r_b, -) per body.  Shared by the allocation and the kernels.
-__host__ __device__ constexpr int x32_stride(int B) { return 12 + 4 * B; }
+// Floats per node of an FP32 record (mixed precision), in float4 groups.
+// New segment (k_fp32): (r_K, mu_c/|r_K|^3), (v_K, -), (indirect term, -),
+// then one (r_K - r_b, -) per body from float 12.  Correction solve
+// (k_corr32): (r, mu_c/|r|^3), (v, -), (residual 0..3), (residual 4..5, -, -),
+// then one (r - r_b, mu_b/|r - r_b|^3) per body from float 16.  Shared by the
+// allocation and the kernels.
+__host__ __device__ constexpr int x32_stride(int B) { return 16 + 4 * B; }
 
 // Trajectory phases: FP64 sweeps, finished, FP32 sweeps (mixed precision).
 // PH_READY64: the FP32 phase ended in this round's k_fp32; the control kernel
 // moves the trajectory to PH_ITER and onto the next round's FP64 list.
-enum : int { PH_ITER = 0, PH_DONE = 1, PH_ITER32 = 2, PH_READY64 = 3 };
+// PH_CORR32: after an FP64 sweep, the next round's k_corr32 solves in FP32 for
+// the correction to the iterate, then the trajectory goes PH_READY64.
+enum : int { PH_ITER = 0, PH_DONE = 1, PH_ITER32 = 2, PH_READY64 = 3, PH_CORR32 = 4 };
 
 // Segment-attempt outcomes.
 enum : int { SEG_CONTINUE = -1, SEG_OK = 0, SEG_STALLED = 1, SEG_FAIL_CAP = 2, SEG_FAIL_DIV = 3, SEG_FAIL_TRUNC = 4 };
@@ -51,9 +56,10 @@ struct Ctl {
   long long *p;       // segment start, in units of hbase / 2^max_depth
   int *depth, *phase, *status, *sweeps, *seg_sweeps, *nstall, *nseg, *need_setup, *last, *ic;
   unsigned *err32;    // final FP32-phase change of a trajectory whose FP32 phase blew up
+  int *ncorr;         // FP32 correction solves in the current segment attempt
 };
 constexpr int kCtlDoubles = 16;  // x[6] + t0, tf, total, sgn, hbase, ta, tb, w1, w2, e_best
-constexpr int kCtlInts = 11;     // 10 ints + err32
+constexpr int kCtlInts = 12;     // 10 ints + err32 + ncorr
 
 // Sweep parameters of one call.
 struct Sweep {
@@ -72,6 +78,9 @@ struct Sweep {
   double tol, stall_factor, div_limit, trunc_tol;
   int mixed;                 // 1: segments start with FP32 sweeps
   double switch_tol;         // FP32 -> FP64 when the FP32 change is below this
+  int refine;                // 1: FP32 correction solves between FP64 sweeps
+  int max_corr;              // correction solves per segment attempt
+  double corr_hi;            // an FP64 change below this may be followed by a correction solve
   int max_ckpt;
   double *ckpt;              // [n_ic][max_ckpt][7] or nullptr
   // adjoint checkpoints: per trajectory and accepted segment k < tape_seg a record
@@ -87,6 +96,8 @@ struct Sweep {
   int *list_cnt;             // [2]
   int *l64[2];               // trajectories doing an FP64 sweep
   int *l64_cnt;              // [2]
+  int *lc[2];                // trajectories doing an FP32 correction solve
+  int *lc_cnt;               // [2]
   int list_cur;
   int *tile_ctr;             // dynamic tile counter of the FP64 contraction
   unsigned long long *cnt64; // [0] FP64, [1] FP32 trajectory-sweeps of this call
@@ -103,11 +114,13 @@ struct Workspace {
   // mixed precision (allocated when the plan asks for it), by new-segment list entry
   double *YK = nullptr;      // [entry][n][6] FP64 warm start
   float *X32 = nullptr;      // [entry][n][x32_stride(B)] FP32 node records
+  float *R32[2] = {nullptr, nullptr};   // [n][6][ld] FP64 sweep residual Y' - Y, rounded (+ repack target)
   Ctl ctl[2]{};              // live control state and repack target
   void *ctl_block[2] = {nullptr, nullptr};
-  int *lists = nullptr;      // 4 x ld: setup lists [2], FP64 lists [2]
+  int *lists = nullptr;      // 6 x ld: setup lists [2], FP64 lists [2], correction lists [2]
   int *ints = nullptr;       // [0..1] done counters [finished, stopped], [2..3] setup list counts,
-                             // [4] repack count, [5..6] FP64 list counts, [7] tile counter
+                             // [4] repack count, [5..6] FP64 list counts, [7] tile counter,
+                             // [8..9] correction list counts
   int *pos = nullptr;        // [ld] repack destinations
   unsigned long long *cnt64 = nullptr;  // [0] FP64 trajectory-sweeps, [1] FP32 trajectory-sweeps
   unsigned long long *h_cnt64 = nullptr;
@@ -141,7 +154,7 @@ struct pc_plan {
   int N = 0, n = 0, kpad = 0, rows_pad = 0;
   int segments = 0;
   pc_options opt{};
-  pc_tuning tune{4, 1, 4, 8, 8, 1, 1};
+  pc_tuning tune{4, 4, 4, 8, 8, 1, 1};
   long long session_id = 0;  // distinguishes calls for the graph cache
   int device = 0;
   // model (device copies)

@@ -84,6 +84,7 @@ extern "C" pc_status pc_options_default(pc_options *o) {
   o->precision = PC_PREC_FP64;
   o->switch_tol = 0.0;
   o->max_rounds = 0;
+  o->refine32 = 1;
   return PC_OK;
 }
 
@@ -91,7 +92,7 @@ static pc_status check_options(const pc_options &o) {
   if (!(o.tol >= 0.0) || o.max_iters < 1 || o.max_depth < 0 || o.max_depth > 30 || o.stall_sweeps < 1 ||
       !(o.stall_factor >= 0.0) || !(o.div_limit > 0.0) || (o.seg_mode != 0 && o.seg_mode != 1) ||
       (o.precision != PC_PREC_FP64 && o.precision != PC_PREC_MIXED) || o.max_rounds < 0 ||
-      !(o.switch_tol >= 0.0))
+      !(o.switch_tol >= 0.0) || (o.refine32 != 0 && o.refine32 != 1))
     return PC_EINVAL;
   return PC_OK;
 }
@@ -227,6 +228,7 @@ void carve_ctl(void *block, long long ld, Ctl &t) {
   t.last = (int *)take(4);
   t.ic = (int *)take(4);
   t.err32 = (unsigned *)take(4);
+  t.ncorr = (int *)take(4);
 }
 }  // namespace
 
@@ -253,8 +255,9 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic, int mixed) {
   if (mixed && e == cudaSuccess) {
     e = dalloc(&w.YK, n * 6 * ld);
     if (e == cudaSuccess) e = dalloc(&w.X32, n * (size_t)x32_stride((int)B) * ld);
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc(&w.R32[b], n * 6 * ld);
   }
-  if (e == cudaSuccess) e = dalloc(&w.lists, 4 * ld);
+  if (e == cudaSuccess) e = dalloc(&w.lists, 6 * ld);
   if (e == cudaSuccess) e = dalloc(&w.pos, ld);
   if (e == cudaSuccess) e = dalloc(&w.cnt64, 2);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&w.h_cnt64, sizeof(unsigned long long) * 2);
@@ -284,6 +287,7 @@ void pcx::free_workspace(pc_plan *p) {
   }
   cudaFree(w.YK);
   cudaFree(w.X32);
+  for (int b = 0; b < 2; b++) cudaFree(w.R32[b]);
   cudaFree(w.G);
   cudaFree(w.tails);
   cudaFree(w.lists);

@@ -72,6 +72,7 @@ __device__ void schedule(const Sweep &s, Ctl &c, int m, int list_next) {
   c.need_setup[m] = 1;
   c.seg_sweeps[m] = 0;
   c.nstall[m] = 0;
+  c.ncorr[m] = 0;
   c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);  // +inf
   c.phase[m] = s.mixed ? PH_ITER32 : PH_ITER;
   const int k = atomicAdd(s.list_cnt + list_next, 1);
@@ -236,6 +237,7 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     s.list_cnt[cur ^ 1] = 0;
     s.l64_cnt[cur ^ 1] = 0;
+    s.lc_cnt[cur ^ 1] = 0;
   }
   const long long count = s.list_cnt[cur];
   const int *__restrict__ list = s.list[cur];
@@ -408,7 +410,8 @@ template <bool DIAG>
 __device__ __forceinline__ void contract_tile_split(const Sweep &s, const Ctl &c, const double *__restrict__ K,
                                                     const double *__restrict__ G, const double *__restrict__ Yold,
                                                     double *__restrict__ Ynew, int rt, int e0, int ncols,
-                                                    const int *__restrict__ map, double *part) {
+                                                    const int *__restrict__ map, double *part,
+                                                    float *__restrict__ R32) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int ld = s.ld;
@@ -475,6 +478,9 @@ __device__ __forceinline__ void contract_tile_split(const Sweep &s, const Ctl &c
           double d[6];
 #pragma unroll
           for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
+          if (R32)  // the sweep's residual, for an FP32 correction solve next round
+#pragma unroll
+            for (int q = 0; q < 6; q++) R32[base + (size_t)q * ld] = (float)d[q];
           double dr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
           double dv = sqrt(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
           if (s.relative) {
@@ -516,7 +522,8 @@ __device__ __forceinline__ void contract_tile_split(const Sweep &s, const Ctl &c
 // in L1/L2) from a counter that the round's setup kernel cleared.
 __global__ void __launch_bounds__(32 * kSplit) k_contract(Sweep s, Ctl c, const double *__restrict__ K,
                                                           const double *__restrict__ G,
-                                                          const double *__restrict__ Yold, double *__restrict__ Ynew) {
+                                                          const double *__restrict__ Yold, double *__restrict__ Ynew,
+                                                          float *__restrict__ R32) {
   __shared__ double part[(kSplit - 1) * 32 * 24];
   __shared__ int tile_sh;
   const int ncols = s.l64_cnt[s.list_cur];
@@ -529,7 +536,7 @@ __global__ void __launch_bounds__(32 * kSplit) k_contract(Sweep s, Ctl c, const 
     const int tile = tile_sh;
     __syncthreads();
     if (tile >= n_tiles) break;
-    contract_tile_split<false>(s, c, K, G, Yold, Ynew, tile % n_rt, (tile / n_rt) * 8, ncols, map, part);
+    contract_tile_split<false>(s, c, K, G, Yold, Ynew, tile % n_rt, (tile / n_rt) * 8, ncols, map, part, R32);
   }
 }
 
@@ -542,203 +549,208 @@ __global__ void __launch_bounds__(32 * kSplit) k_contract_diag(Sweep s, Ctl c, c
   const int ncols = (int)s.n_ic;
   const int n_tiles = n_rt * ((ncols + 7) / 8);
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
-    contract_tile_split<true>(s, c, K, G, nullptr, Ynew, tile % n_rt, (tile / n_rt) * 8, ncols, nullptr, part);
+    contract_tile_split<true>(s, c, K, G, nullptr, Ynew, tile % n_rt, (tile / n_rt) * 8, ncols, nullptr, part,
+                              nullptr);
 }
 
 // ---------------------------------------------------------------------------
-// FP32 phase (mixed precision, an extension of the paper).  The iterate is
-// written y = y_K + delta with y_K the FP64 warm start of the segment.  The
-// Picard map gives delta' = rho + omega2 K (f(y_K + delta) - f_K), with f_K the
-// two-body derivative of y_K and rho = x0 + omega2 K f_K - y_K the operator's
-// residual on the Kepler arc (below the resolution tolerance on accepted
-// segments; dropped in this phase and restored by the FP64 sweeps that
-// follow).  The force deviation is formed without cancellation (Encke):
+// FP32 sweeps (mixed precision, an extension of the paper), two modes.
+//
+// KEPLER (new segments): the iterate is y = y_K + delta with y_K the FP64
+// warm start.  The Picard map gives delta' = rho + omega2 K (f(y_K + delta) -
+// f_K), with f_K the two-body derivative of y_K and rho = x0 + omega2 K f_K -
+// y_K the operator's residual on the Kepler arc (below the resolution
+// tolerance on accepted segments; dropped here and restored by the FP64
+// sweeps that follow).  The central force deviation is formed without
+// cancellation (Encke):
 //   (mu_c/|r_K|^3) [F(q) (r_K + dr) - dr],  q = dr.(2 r_K + dr)/|r_K|^2,
 //   F = 1 - (1+q)^(-3/2) = q s^2 (1 + s + s^2)/(1 + s),  s = (1+q)^(-1/2),
 // plus the bodies' terms with r - r_b = (r_K - r_b) + dr, where r_K - r_b was
 // formed in FP64 before rounding.  Its rounding error is relative to |delta|,
 // not to |y|.
+//
+// CORRECTION (iterative refinement): an FP64 sweep took the iterate Y to
+// Y' = x0 + omega2 K G(Y) with residual R = Y' - Y (kept rounded to FP32).  The
+// fixed point Y* satisfies Y* = Y + c with c = R + omega2 K [G(Y + c) - G(Y)],
+// solved about the base Y = Y' - R (formed in FP64): the central and every
+// body term as Encke differences (base-to-body vectors formed in FP64 then
+// rounded), the velocity rows as omega2 c_v.  Then Y* = Y' + omega2 K [G(Y + c)
+// - G(Y)] (the last sweep's contraction) is written in FP64.
+//
+// One CTA per trajectory, one thread per node (the CTA has 32 ceil((N+1)/32)
+// threads): a thread keeps its node's deviation in registers across sweeps,
+// writes its force row into the CTA's table in shared memory, and forms its
+// row of the contraction from K (read coalesced, L1-resident) and the table
+// (broadcast reads).  The sweeps stop when the change is below the FP32 floor
+// (or switch_tol, KEPLER), fails to halve the best change for two sweeps, or
+// reaches max_iters.  Then the result goes to the next round's buffer and the
+// control kernel puts the trajectory on the next round's FP64 list.  A
+// non-finite or huge change: KEPLER leaves the trajectory in the FP32 phase
+// with that change and the control kernel halves the segment; CORRECTION
+// keeps Y' and allows no further corrections in this segment attempt.
 // ---------------------------------------------------------------------------
-// One warp per new segment (list entry e, slot m).  Lane l owns nodes
-// j = l + 32 i, i < NPL: it builds their force deviations and accumulates their
-// rows of the contraction, so the deviation stays in registers across sweeps;
-// the warp's force table F32[j][6] is shared through shared memory, and the
-// block stages the FP32 operator K32T ([N+1][32 NPL], transposed) in shared
-// memory when KSMEM.  The sweeps stop when the change is below switch_tol or
-// the FP32 floor, fails to halve the best change for two sweeps, or reaches
-// max_iters: then Y = y_K + delta is written to the next round's buffer and
-// the control kernel puts the trajectory on the next round's FP64 list.  A
-// non-finite or huge change leaves the trajectory in the FP32 phase with that
-// change, and the control kernel halves the segment.  Four warps per CTA keep
-// a CTA's registers (at most 128 per thread) and shared memory small enough to
-// sit beside the FP64 branch's CTAs, which run at the same time.
-constexpr int kFp32Warps = 4;
 constexpr float kFp32Floor = 2e-6f;
+constexpr int kFp32MaxThreads = 288;  // N + 1 <= 288
+enum : int { FP32_KEPLER = 0, FP32_CORR = 1 };
 
-template <int NPL, bool KSMEM>
-__global__ void __launch_bounds__(32 * kFp32Warps, 4) k_fp32(Sweep s, Ctl c, Model md, const float *__restrict__ K32T,
-                                                        const float *__restrict__ mu32, double *__restrict__ Y,
-                                                        Mix mx) {
-  extern __shared__ float4 fp32_smem4[];
-  float *sm = reinterpret_cast<float *>(fp32_smem4);
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int N = s.N, n = s.n, ld = s.ld, B = md.B, np = 32 * NPL;
-  // With KSMEM the operator is staged per lane: Ks[l * lstride + i * n4 + k] =
-  // K[l + 32 i][k], k padded to n4 = 4 ceil(n/4) with zeros, and
-  // lstride = 32 ceil(NPL n4 / 32) + 4 so that the 16-byte loads of 8
-  // consecutive lanes hit distinct bank groups.  Each lane then reads four
-  // k-values of a row with one 16-byte load.
-  const int n4 = (n + 3) & ~3;
-  const int lstride = ((NPL * n4 + 31) & ~31) + 4;
-  const float *Kt = K32T;
-  float *Gs;
-  if (KSMEM) {
-    float *Ks = sm;
-    for (int idx = threadIdx.x; idx < 32 * NPL * n4; idx += blockDim.x) {
-      const int k = idx % n4, li = idx / n4;  // li = l * NPL + i
-      const int l = li / NPL, i = li % NPL;
-      Ks[l * lstride + i * n4 + k] = (k < n) ? K32T[(size_t)k * np + l + 32 * i] : 0.0f;
-    }
-    Kt = Ks;
-    Gs = sm + (size_t)32 * lstride + (size_t)wib * n4 * 6;
-    for (int k = n + lane; k < n4; k += 32)
-      for (int q = 0; q < 6; q++) Gs[k * 6 + q] = 0.0f;
-    __syncthreads();
-  } else {
-    Gs = sm + (size_t)wib * n * 6;
-  }
+__device__ __forceinline__ float encke_F(float q) {
+  const float sq = rsqrtf(1.0f + q);
+  return q * sq * sq * (1.0f + sq + sq * sq) / (1.0f + sq);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model md, const float *__restrict__ K32T,
+                                                        const float *__restrict__ mu32, const double *__restrict__ Yc,
+                                                        double *__restrict__ Yn, const double *__restrict__ E,
+                                                        const float *__restrict__ R32, Mix mx) {
+  extern __shared__ float fp32_sm[];
+  float *Gs = fp32_sm;                          // [n][6] force table of the CTA's trajectory
+  float *red = fp32_sm + (size_t)s.n * 6;      // [2][warps] change / size partial maxima
+  const int j = threadIdx.x, lane = j & 31, warp = j >> 5, nw = blockDim.x >> 5;
+  const int N = s.N, n = s.n, ld = s.ld, B = md.B, np = 32 * ((N + 32) / 32);
+  const bool node = j <= N;
   const int cur = s.list_cur;
-  const int count = s.list_cnt[cur];
-  // entries go to blocks first (e = wib * gridDim.x + blockIdx.x), so a round
-  // with few new segments still spreads them over every SM
-  for (int e = wib * gridDim.x + blockIdx.x; e < count; e += gridDim.x * kFp32Warps) {
-    const int m = s.list[cur][e];
+  const int count = MODE == FP32_KEPLER ? s.list_cnt[cur] : s.lc_cnt[cur];
+  const int *list = MODE == FP32_KEPLER ? s.list[cur] : s.lc[cur];
+  const int boff = MODE == FP32_KEPLER ? 3 : 4;  // float4 index of the first body record
+  const float muc = (float)md.mu_c;
+  for (int e = blockIdx.x; e < count; e += gridDim.x) {
+    const int m = list[e];
     const float w2f = (float)c.w2[m];
-    const float *recs = mx.X32 + (size_t)e * n * mx.xs;
-    float dl[NPL][6];
+    const float4 *rc = reinterpret_cast<const float4 *>(mx.X32 + ((size_t)e * n + (node ? j : 0)) * mx.xs);
+    const size_t yb = (size_t)j * 6 * ld + m;
+    if (MODE == FP32_CORR && node) {
+      // node record from the FP64 iterate, its residual and the body positions
+      float4 *wc = reinterpret_cast<float4 *>(mx.X32 + ((size_t)e * n + j) * mx.xs);
+      double base[6];
+      float res[6];
 #pragma unroll
-    for (int i = 0; i < NPL; i++)
-#pragma unroll
-      for (int q = 0; q < 6; q++) dl[i][q] = 0.0f;
-    float ebest = __int_as_float(0x7f800000);
+      for (int q = 0; q < 6; q++) {
+        res[q] = (j == 0) ? 0.0f : R32[yb + (size_t)q * ld];
+        base[q] = Yc[yb + (size_t)q * ld] - (double)res[q];
+      }
+      const float bx = (float)base[0], by = (float)base[1], bz = (float)base[2];
+      const float ir = rsqrtf(bx * bx + by * by + bz * bz);
+      wc[0] = make_float4(bx, by, bz, muc * ir * ir * ir);
+      wc[1] = make_float4((float)base[3], (float)base[4], (float)base[5], 0.0f);
+      wc[2] = make_float4(res[0], res[1], res[2], res[3]);
+      wc[3] = make_float4(res[4], res[5], 0.0f, 0.0f);
+      for (int b = 0; b < B; b++) {
+        const double *eb = E + (size_t)(j * B + b) * 3 * ld + m;
+        const float dx = (float)(base[0] - eb[0]), dy = (float)(base[1] - eb[(size_t)ld]),
+                    dz = (float)(base[2] - eb[(size_t)2 * ld]);
+        const float id = rsqrtf(dx * dx + dy * dy + dz * dz);
+        wc[4 + b] = make_float4(dx, dy, dz, mu32[b] * id * id * id);
+      }
+      __threadfence_block();
+    }
+    float dl[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acc[6];
+    float res[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (MODE == FP32_CORR && node) {
+      const float4 r0 = rc[2], r1 = rc[3];
+      res[0] = r0.x; res[1] = r0.y; res[2] = r0.z; res[3] = r0.w; res[4] = r1.x; res[5] = r1.y;
+    }
+    float ebest = __int_as_float(0x7f800000), efin = 0.0f;
     int nst = 0, it = 0;
     bool fail = false;
-    float efin = 0.0f;
     for (;;) {
-      // force deviation at the lane's nodes
-#pragma unroll
-      for (int i = 0; i < NPL; i++) {
-        const int j = lane + 32 * i;
-        if (j > N) break;
-        const float4 *rc = reinterpret_cast<const float4 *>(recs + (size_t)j * mx.xs);
+      // force deviation at this thread's node
+      if (node) {
         const float4 rk = rc[0];
-        const float d0 = dl[i][0], d1 = dl[i][1], d2 = dl[i][2];
+        const float d0 = dl[0], d1 = dl[1], d2 = dl[2];
         const float rr = rk.x * rk.x + rk.y * rk.y + rk.z * rk.z;
-        const float qn = (d0 * (2.0f * rk.x + d0) + d1 * (2.0f * rk.y + d1) + d2 * (2.0f * rk.z + d2)) / rr;
-        const float sq = rsqrtf(1.0f + qn);
-        const float F = qn * sq * sq * (1.0f + sq + sq * sq) / (1.0f + sq);
+        const float F = encke_F((d0 * (2.0f * rk.x + d0) + d1 * (2.0f * rk.y + d1) + d2 * (2.0f * rk.z + d2)) / rr);
         float a0 = rk.w * (F * (rk.x + d0) - d0);
         float a1 = rk.w * (F * (rk.y + d1) - d1);
         float a2 = rk.w * (F * (rk.z + d2) - d2);
         for (int b = 0; b < B; b++) {
-          const float4 D = rc[3 + b];
-          const float x0 = D.x + d0, x1 = D.y + d1, x2 = D.z + d2;
-          const float ds = rsqrtf(x0 * x0 + x1 * x1 + x2 * x2);
-          const float kb = mu32[b] * ds * ds * ds;
-          a0 -= kb * x0;
-          a1 -= kb * x1;
-          a2 -= kb * x2;
+          const float4 D = rc[boff + b];
+          if (MODE == FP32_KEPLER) {
+            const float x0 = D.x + d0, x1 = D.y + d1, x2 = D.z + d2;
+            const float ds = rsqrtf(x0 * x0 + x1 * x1 + x2 * x2);
+            const float kb = mu32[b] * ds * ds * ds;
+            a0 -= kb * x0;
+            a1 -= kb * x1;
+            a2 -= kb * x2;
+          } else {
+            const float dd = D.x * D.x + D.y * D.y + D.z * D.z;
+            const float Fb = encke_F((d0 * (2.0f * D.x + d0) + d1 * (2.0f * D.y + d1) + d2 * (2.0f * D.z + d2)) / dd);
+            a0 += D.w * (Fb * (D.x + d0) - d0);
+            a1 += D.w * (Fb * (D.y + d1) - d1);
+            a2 += D.w * (Fb * (D.z + d2) - d2);
+          }
         }
-        if (md.indirect) {
+        if (MODE == FP32_KEPLER && md.indirect) {
           const float4 ai = rc[2];
           a0 -= ai.x;
           a1 -= ai.y;
           a2 -= ai.z;
         }
         float2 *g = reinterpret_cast<float2 *>(Gs + (size_t)j * 6);
-        g[0] = make_float2(w2f * dl[i][3], w2f * dl[i][4]);
-        g[1] = make_float2(w2f * dl[i][5], w2f * a0);
+        g[0] = make_float2(w2f * dl[3], w2f * dl[4]);
+        g[1] = make_float2(w2f * dl[5], w2f * a0);
         g[2] = make_float2(w2f * a1, w2f * a2);
       }
-      __syncwarp();
-      float acc[NPL][6];
+      __syncthreads();
+      // this node's row of the contraction
 #pragma unroll
-      for (int i = 0; i < NPL; i++)
-#pragma unroll
-        for (int q = 0; q < 6; q++) acc[i][q] = 0.0f;
-      if (KSMEM) {
-        const float *kl = Kt + (size_t)lane * lstride;
-        for (int k = 0; k < n4; k += 4) {
-          float4 kv[NPL];
-#pragma unroll
-          for (int i = 0; i < NPL; i++) kv[i] = *reinterpret_cast<const float4 *>(kl + i * n4 + k);
-          const float4 *g4 = reinterpret_cast<const float4 *>(Gs + k * 6);
-          float g[24];
-#pragma unroll
-          for (int v = 0; v < 6; v++) {
-            const float4 t4 = g4[v];
-            g[4 * v] = t4.x;
-            g[4 * v + 1] = t4.y;
-            g[4 * v + 2] = t4.z;
-            g[4 * v + 3] = t4.w;
-          }
-#pragma unroll
-          for (int i = 0; i < NPL; i++) {
-            const float kk[4] = {kv[i].x, kv[i].y, kv[i].z, kv[i].w};
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-#pragma unroll
-              for (int q = 0; q < 6; q++) acc[i][q] = fmaf(kk[u], g[6 * u + q], acc[i][q]);
-          }
-        }
-      } else {
-#pragma unroll 2
+      for (int q = 0; q < 6; q++) acc[q] = 0.0f;
+      if (node) {
+        const float *kr = K32T + j;
+#pragma unroll 4
         for (int k = 0; k < n; k++) {
+          const float kv = __ldg(kr + (size_t)k * np);
           const float2 *g2 = reinterpret_cast<const float2 *>(Gs + k * 6);
           const float2 ga = g2[0], gb = g2[1], gc = g2[2];
-          const float g[6] = {ga.x, ga.y, gb.x, gb.y, gc.x, gc.y};
-          const float *kr = Kt + (size_t)k * np + lane;
-#pragma unroll
-          for (int i = 0; i < NPL; i++) {
-            const float kv = __ldg(kr + 32 * i);
-#pragma unroll
-            for (int q = 0; q < 6; q++) acc[i][q] = fmaf(kv, g[q], acc[i][q]);
-          }
+          acc[0] = fmaf(kv, ga.x, acc[0]);
+          acc[1] = fmaf(kv, ga.y, acc[1]);
+          acc[2] = fmaf(kv, gb.x, acc[2]);
+          acc[3] = fmaf(kv, gb.y, acc[3]);
+          acc[4] = fmaf(kv, gc.x, acc[4]);
+          acc[5] = fmaf(kv, gc.y, acc[5]);
         }
       }
-      __syncwarp();
+      // change and size of the deviation, relative to the iterate
       float emax = 0.0f, dmax = 0.0f;
-#pragma unroll
-      for (int i = 0; i < NPL; i++) {
-        const int j = lane + 32 * i;
-        if (j > N) break;
-        const float4 *rc = reinterpret_cast<const float4 *>(recs + (size_t)j * mx.xs);
+      if (node) {
         const float4 rk = rc[0], vk = rc[1];
         const float yk[6] = {rk.x, rk.y, rk.z, vk.x, vk.y, vk.z};
-        float d[6], y[6];
+        float d[6], y[6], cn[6];
 #pragma unroll
         for (int q = 0; q < 6; q++) {
-          d[q] = acc[i][q] - dl[i][q];
-          y[q] = yk[q] + acc[i][q];
-          dl[i][q] = acc[i][q];
+          cn[q] = res[q] + acc[q];
+          d[q] = cn[q] - dl[q];
+          y[q] = yk[q] + cn[q];
+          dl[q] = cn[q];
         }
         float dr = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         float dv = sqrtf(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
-        float mr = sqrtf(acc[i][0] * acc[i][0] + acc[i][1] * acc[i][1] + acc[i][2] * acc[i][2]);
-        float mv = sqrtf(acc[i][3] * acc[i][3] + acc[i][4] * acc[i][4] + acc[i][5] * acc[i][5]);
+        float mr = sqrtf(cn[0] * cn[0] + cn[1] * cn[1] + cn[2] * cn[2]);
+        float mv = sqrtf(cn[3] * cn[3] + cn[4] * cn[4] + cn[5] * cn[5]);
         if (s.relative) {
           const float nr = sqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
           const float nv = sqrtf(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
           if (nr > 0.0f) { dr /= nr; mr /= nr; }
           if (nv > 0.0f) { dv /= nv; mv /= nv; }
         }
-        emax = nanmaxf(emax, nanmaxf(dr, dv));
-        dmax = fmaxf(dmax, fmaxf(mr, mv));
+        emax = nanmaxf(dr, dv);
+        dmax = fmaxf(mr, mv);
       }
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
         emax = nanmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      }
+      if (lane == 0) {
+        red[warp] = emax;
+        red[nw + warp] = dmax;
+      }
+      __syncthreads();
+      emax = 0.0f;
+      dmax = 0.0f;
+      for (int w = 0; w < nw; w++) {
+        emax = nanmaxf(emax, red[w]);
+        dmax = fmaxf(dmax, red[nw + w]);
       }
       it++;
       efin = emax;
@@ -748,39 +760,49 @@ __global__ void __launch_bounds__(32 * kFp32Warps, 4) k_fp32(Sweep s, Ctl c, Mod
       }
       // The FP32 floor: the change cannot fall much below the rounding of the
       // contraction, ~sqrt(N) FP32 ulps of the deviation itself, so a change
-      // under kFp32Floor * max|delta|/|y| ends the phase.  Failing to halve the
-      // best change for two sweeps (fluctuation at the floor) also ends it.
+      // under kFp32Floor * max|deviation|/|y| ends the phase.  Failing to halve
+      // the best change for two sweeps (fluctuation at the floor) also ends it.
       if (emax < 0.5f * ebest) {
         nst = 0;
       } else {
         nst++;
       }
       ebest = fminf(ebest, emax);
-      if ((double)emax < s.switch_tol || emax < kFp32Floor * dmax || nst >= 2 || it >= s.max_iters) break;
+      if ((MODE == FP32_KEPLER && (double)emax < s.switch_tol) || emax < kFp32Floor * dmax || nst >= 2 ||
+          it >= s.max_iters)
+        break;
+      __syncthreads();  // the table is rewritten by the next sweep
     }
-    if (!fail) {
+    if (node) {
+      if (MODE == FP32_KEPLER) {
+        if (!fail) {
+          const double *yk = mx.YK + ((size_t)e * n + j) * 6;
 #pragma unroll
-      for (int i = 0; i < NPL; i++) {
-        const int j = lane + 32 * i;
-        if (j > N) break;
-        const double *yk = mx.YK + ((size_t)e * n + j) * 6;
+          for (int q = 0; q < 6; q++) Yn[yb + (size_t)q * ld] = yk[q] + (double)dl[q];
+        }
+      } else {
 #pragma unroll
-        for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = yk[q] + (double)dl[i][q];
+        for (int q = 0; q < 6; q++) Yn[yb + (size_t)q * ld] = Yc[yb + (size_t)q * ld] + (fail ? 0.0 : (double)acc[q]);
       }
     }
-    if (lane == 0) {
+    if (j == 0) {
       c.sweeps[m] += it;
       atomicAdd(s.cnt64 + 1, (unsigned long long)it);
-      if (fail) {
-        c.err32[m] = err_bits32(efin);
+      if (MODE == FP32_KEPLER) {
+        if (fail) {
+          c.err32[m] = err_bits32(efin);
+        } else {
+          c.phase[m] = PH_READY64;
+          c.seg_sweeps[m] = 0;
+          c.nstall[m] = 0;
+          c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);
+        }
       } else {
+        if (fail) c.ncorr[m] = s.max_corr;
         c.phase[m] = PH_READY64;
-        c.seg_sweeps[m] = 0;
-        c.nstall[m] = 0;
-        c.e_best[m] = __longlong_as_double(0x7FF0000000000000LL);
       }
     }
-    __syncwarp();
+    __syncthreads();  // the table and the partial maxima are reused by the next trajectory
   }
 }
 
@@ -838,6 +860,7 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
   const int ld = s.ld;
   const int list_next = s.list_cur ^ 1;
   int out = SEG_CONTINUE;
+  double e_sweep = 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) *s.tile_ctr = 0;  // this round's contraction is over
   if (ready) {
     c.need_setup[m] = 0;
@@ -852,6 +875,7 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
     if (phase == PH_ITER) {
       c.sweeps[m] += 1;
       const double e = __longlong_as_double((long long)c.err[m]);
+      e_sweep = e;
       c.err[m] = 0ULL;
       const int ss = ++c.seg_sweeps[m];
       if (!(e <= s.div_limit)) {
@@ -923,6 +947,16 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
       }
     }
   }
+  // an FP64 sweep that left the segment unfinished with a small change: solve
+  // for the correction to its iterate in FP32 next round instead of sweeping on
+  bool to_corr = false;
+  if (act && phase == PH_ITER && out == SEG_CONTINUE && s.refine && e_sweep < s.corr_hi &&
+      c.ncorr[m] < s.max_corr) {
+    c.phase[m] = PH_CORR32;
+    c.ncorr[m] += 1;
+    to_corr = true;
+  }
+  warp_append(to_corr, m, s.lc[list_next], s.lc_cnt + list_next);
   const bool next64 = (act && c.phase[m] == PH_ITER) || ready;
   warp_append(next64, m, s.l64[list_next], s.l64_cnt + list_next);
 }
@@ -987,6 +1021,7 @@ __global__ void k_repack_ctl(Sweep s, Ctl a, Ctl b, const int *__restrict__ pos)
     b.last[d] = a.last[m];
     b.ic[d] = a.ic[m];
     b.err32[d] = a.err32[m];
+    b.ncorr[d] = a.ncorr[m];
     if (a.need_setup[m]) {
       const int k = atomicAdd(s.list_cnt + list_next, 1);
       s.list[list_next][k] = d;
@@ -994,6 +1029,7 @@ __global__ void k_repack_ctl(Sweep s, Ctl a, Ctl b, const int *__restrict__ pos)
     to64 = a.phase[m] == PH_ITER;
   }
   warp_append(to64, d, s.l64[list_next], s.l64_cnt + list_next);
+  warp_append(d >= 0 && a.phase[m] == PH_CORR32, d, s.lc[list_next], s.lc_cnt + list_next);
 }
 
 // Round cap reached: remaining trajectories stop with NOT_CONVERGED.
@@ -1058,56 +1094,25 @@ Mix live_mix(const pc_plan *p) {
   return mx;
 }
 
-// The FP32 operator goes to shared memory when it fits beside the force tables.
-constexpr size_t kFp32KsmemLimit = 120 * 1024;
-
 unsigned sm_ctas(const pc_plan *p, int per_sm) { return (unsigned)((p->num_sms > 0 ? p->num_sms : 152) * per_sm); }
 
-template <int NPL>
-void launch_fp32(const pc_plan *p, const Sweep &s, double *Y, const Mix &mx, cudaStream_t st) {
-  const int n4 = (p->n + 3) & ~3;
-  const int lstride = ((NPL * n4 + 31) & ~31) + 4;
-  const size_t k_bytes = (size_t)32 * lstride * sizeof(float);
-  const size_t g_bytes = (size_t)kFp32Warps * n4 * 6 * sizeof(float);
+// FP32 sweeps of one mode over this round's list: CTAs of 32 ceil((N+1)/32) threads.
+template <int MODE>
+void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn, const double *E, const float *R32,
+                 const Mix &mx, cudaStream_t st) {
+  const int threads = 32 * ((p->n + 31) / 32);
+  const size_t smem = sizeof(float) * ((size_t)p->n * 6 + 2 * (threads / 32));
   const Ctl &c = p->ws.ctl[p->ws.live];
-  if (k_bytes + g_bytes <= kFp32KsmemLimit) {
-    k_fp32<NPL, true><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), 32 * kFp32Warps, k_bytes + g_bytes, st>>>(
-        s, c, p->model, p->d_K32T, p->d_mu32, Y, mx);
-  } else {
-    k_fp32<NPL, false><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), 32 * kFp32Warps, g_bytes, st>>>(
-        s, c, p->model, p->d_K32T, p->d_mu32, Y, mx);
-  }
-}
-
-// Shared-memory opt-in of the FP32 warp kernel for this plan's degree.
-template <int NPL>
-cudaError_t prepare_fp32(const pc_plan *p) {
-  const int n4 = (p->n + 3) & ~3;
-  const int lstride = ((NPL * n4 + 31) & ~31) + 4;
-  const size_t k_bytes = (size_t)32 * lstride * sizeof(float);
-  const size_t g_bytes = (size_t)kFp32Warps * n4 * 6 * sizeof(float);
-  if (k_bytes + g_bytes <= kFp32KsmemLimit)
-    return cudaFuncSetAttribute(k_fp32<NPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(k_bytes + g_bytes));
-  return cudaFuncSetAttribute(k_fp32<NPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_bytes);
+  k_fp32<MODE><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), threads, smem, st>>>(s, c, p->model, p->d_K32T, p->d_mu32, Yc,
+                                                                           Yn, E, R32, mx);
 }
 
 }  // namespace
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t prepare_launches(const pc_plan *p) {
-  if (!p->npl) return cudaSuccess;
-  switch (p->npl) {
-    case 1: return prepare_fp32<1>(p);
-    case 2: return prepare_fp32<2>(p);
-    case 3: return prepare_fp32<3>(p);
-    case 4: return prepare_fp32<4>(p);
-    case 5: return prepare_fp32<5>(p);
-    case 6: return prepare_fp32<6>(p);
-    case 7: return prepare_fp32<7>(p);
-    case 8: return prepare_fp32<8>(p);
-    default: return prepare_fp32<9>(p);
-  }
+  (void)p;  // the FP32 kernels' shared memory stays under the default limit
+  return cudaSuccess;
 }
 
 cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cudaStream_t st) {
@@ -1142,19 +1147,9 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   if (ev) cudaEventRecord(ev[0], st);
   k_setup<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
   if (ev) cudaEventRecord(ev[1], st);
-  if (s.mixed) {
-    switch (p->npl) {
-      case 1: launch_fp32<1>(p, s, Yn, mx, sb); break;
-      case 2: launch_fp32<2>(p, s, Yn, mx, sb); break;
-      case 3: launch_fp32<3>(p, s, Yn, mx, sb); break;
-      case 4: launch_fp32<4>(p, s, Yn, mx, sb); break;
-      case 5: launch_fp32<5>(p, s, Yn, mx, sb); break;
-      case 6: launch_fp32<6>(p, s, Yn, mx, sb); break;
-      case 7: launch_fp32<7>(p, s, Yn, mx, sb); break;
-      case 8: launch_fp32<8>(p, s, Yn, mx, sb); break;
-      default: launch_fp32<9>(p, s, Yn, mx, sb); break;
-    }
-  }
+  float *R32 = s.refine ? w.R32[w.live] : nullptr;
+  if (s.mixed) launch_fp32<FP32_KEPLER>(p, s, Yc, Yn, E, R32, mx, sb);
+  if (s.refine) launch_fp32<FP32_CORR>(p, s, Yc, Yn, E, R32, mx, sb);
   if (branches) {
     e = cudaEventRecord(p->branch_ev[1], sb);
     if (e != cudaSuccess) return e;
@@ -1166,7 +1161,7 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   // persistent FP64 contraction: contract_ctas_per_sm CTAs of kSplit warps per SM
   const long long tiles = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
   const long long blocks = std::max<long long>(1, std::min<long long>(sm_ctas(p, p->tune.contract_ctas_per_sm), tiles));
-  k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn);
+  k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn, R32);
   if (branches) {
     e = cudaStreamWaitEvent(st, p->branch_ev[1], 0);
     if (e != cudaSuccess) return e;
@@ -1175,7 +1170,7 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   // one warp per block: the control work (resolution tests) spreads over all SMs
   k_control<<<blocks_for(s.A, 32), 32, 0, st>>>(s, c, w.tails, Yn, w.ints);
   if (ev) cudaEventRecord(ev[5], st);
-  p->acc_launches += s.mixed ? 5 : 4;
+  p->acc_launches += s.mixed ? (s.refine ? 6 : 5) : 4;
   return cudaGetLastError();
 }
 
@@ -1186,6 +1181,7 @@ cudaError_t launch_repack(const pc_plan *p, const Sweep &s, int cur, cudaStream_
   cudaError_t e = cudaMemsetAsync(w.ints + 4, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.list_cnt + s.list_cur, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.l64_cnt + s.list_cur, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.lc_cnt + s.list_cur, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   const unsigned nb = blocks_for(s.A, kThreads);
   k_repack_pos<<<nb, kThreads, 0, st>>>(s.A, w.ctl[a].phase, w.pos, w.ints + 4);
@@ -1194,8 +1190,9 @@ cudaError_t launch_repack(const pc_plan *p, const Sweep &s, int cur, cudaStream_
   k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 6, w.pos, w.Y[cur], w.Y[cur ^ 1]);
   if (B > 0) k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * B * 3, w.pos, w.E[a], w.E[b]);
   k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 3, w.pos, w.Aind[a], w.Aind[b]);
+  if (s.refine) k_repack_rows<float><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 6, w.pos, w.R32[a], w.R32[b]);
   k_repack_ctl<<<nb, kThreads, 0, st>>>(s, w.ctl[a], w.ctl[b], w.pos);
-  p->acc_launches += 4 + (B > 0);
+  p->acc_launches += 4 + (B > 0) + (s.refine ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -64,7 +64,8 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("relative", C.c_int), ("max_iters", C.c_int), ("max_depth", C.c_int),
                 ("warm_start", C.c_int), ("seg_mode", C.c_int), ("truncated", C.c_int), ("stall_sweeps", C.c_int),
                 ("stall_factor", C.c_double), ("div_limit", C.c_double), ("trunc_tol", C.c_double),
-                ("precision", C.c_int), ("switch_tol", C.c_double), ("max_rounds", C.c_longlong)]
+                ("precision", C.c_int), ("switch_tol", C.c_double), ("max_rounds", C.c_longlong),
+                ("refine32", C.c_int)]
 
 
 def lib():

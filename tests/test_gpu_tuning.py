@@ -41,7 +41,7 @@ def test_tunings_and_graphs_are_bitwise_neutral(pc, precision):
     base = _run(pc, plan, w, x0d, tf)
     assert base[0] in (pc.PC_OK, pc.PC_ENOTCONV)
     settings = [dict(graphs=0), dict(graphs=1, rounds_per_batch=2), dict(contract_ctas_per_sm=1, setup_ctas_per_sm=1),
-                dict(contract_ctas_per_sm=8, fp32_ctas_per_sm=4, setup_ctas_per_sm=16),
+                dict(contract_ctas_per_sm=8, fp32_ctas_per_sm=16, setup_ctas_per_sm=16),
                 dict(repack_div=2, rounds_per_batch=16), dict(repack_div=64, rounds_per_batch=5, graphs=1),
                 dict(side_priority=0, contract_ctas_per_sm=16)]
     for kw in settings:
@@ -49,7 +49,7 @@ def test_tunings_and_graphs_are_bitwise_neutral(pc, precision):
         r = _run(pc, plan, w, x0d, tf)
         for a, b in zip(base[2:], r[2:]):
             assert torch.equal(a, b), kw
-        pc.set_tuning(plan, setup_ctas_per_sm=4, fp32_ctas_per_sm=1, contract_ctas_per_sm=4, rounds_per_batch=8,
+        pc.set_tuning(plan, setup_ctas_per_sm=4, fp32_ctas_per_sm=4, contract_ctas_per_sm=4, rounds_per_batch=8,
                       repack_div=8, graphs=1, side_priority=1)
     # the caller's own (non-default) stream: no fork, graph captured on it directly
     s = torch.cuda.Stream()
@@ -64,10 +64,10 @@ def test_tuning_validation(pc):
     w = W.config1(M=8)
     plan = pc.plan_from_workload(w)
     for bad in (dict(setup_ctas_per_sm=0), dict(contract_ctas_per_sm=17), dict(rounds_per_batch=0),
-                dict(repack_div=1), dict(graphs=2), dict(fp32_ctas_per_sm=9), dict(side_priority=2)):
+                dict(repack_div=1), dict(graphs=2), dict(fp32_ctas_per_sm=17), dict(side_priority=2)):
         with pytest.raises(pc.PCError):
             pc.set_tuning(plan, **bad)
-    assert pc.get_tuning(plan) == dict(setup_ctas_per_sm=4, fp32_ctas_per_sm=1, contract_ctas_per_sm=4,
+    assert pc.get_tuning(plan) == dict(setup_ctas_per_sm=4, fp32_ctas_per_sm=4, contract_ctas_per_sm=4,
                                        rounds_per_batch=8, repack_div=8, graphs=1, side_priority=1)
     plan.close()
 
