@@ -520,7 +520,7 @@ extern "C" pc_status pc_plan_autotune(pc_plan *p, long long n_ic, const double *
   };
   const std::vector<Axis> axes = {
       {&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8, 12, 16}},
-      {&pc_tuning::setup_ctas_per_sm, {1, 2, 4, 8}},
+      {&pc_tuning::setup_ctas_per_sm, {2, 4, 8, 16}},
       {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{2, 4, 6, 8, 12} : std::vector<int>{}},
       {&pc_tuning::side_priority, mixed ? std::vector<int>{0, 1} : std::vector<int>{}},
       {&pc_tuning::rounds_per_batch, {4, 8, 16, 32}},

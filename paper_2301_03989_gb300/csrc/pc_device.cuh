@@ -53,6 +53,18 @@ constexpr int kEphemMaxCoefs = 64;  // degrees up to 63
 
 // Calls out(b, r) for every body b in order with its position r[3].
 template <class Out>
+__device__ __forceinline__ void ephem_all(const Model &md, EphemLoc L, Out out);
+
+// Same for the bodies b_lo <= b < b_hi.
+template <class Out>
+__device__ __forceinline__ void ephem_range(const Model &md, EphemLoc L, int b_lo, int b_hi, Out out) {
+  Model sub = md;
+  sub.coef = md.coef + (size_t)b_lo * md.n_gr * 3 * (md.deg + 1);
+  sub.B = b_hi - b_lo;
+  ephem_all(sub, L, [&](int b, const double r[3]) { out(b_lo + b, r); });
+}
+
+template <class Out>
 __device__ __forceinline__ void ephem_all(const Model &md, EphemLoc L, Out out) {
   const int nc = md.deg + 1;
   const double s2 = 2.0 * L.sig;

@@ -580,8 +580,8 @@ __global__ void __launch_bounds__(32 * kSplit) k_contract_diag(Sweep s, Ctl c, c
 // One CTA per trajectory, one thread per node (the CTA has 32 ceil((N+1)/32)
 // threads): a thread keeps its node's deviation in registers across sweeps,
 // writes its force row into the CTA's table in shared memory, and forms its
-// row of the contraction from K (read coalesced, L1-resident) and the table
-// (broadcast reads).  The sweeps stop when the change is below the FP32 floor
+// row of the contraction from K (read coalesced) and the table (broadcast
+// reads); the trajectory's node records sit in shared memory for all sweeps.  The sweeps stop when the change is below the FP32 floor
 // (or switch_tol, KEPLER), fails to halve the best change for two sweeps, or
 // reaches max_iters.  Then the result goes to the next round's buffer and the
 // control kernel puts the trajectory on the next round's FP64 list.  A
@@ -591,6 +591,10 @@ __global__ void __launch_bounds__(32 * kSplit) k_contract_diag(Sweep s, Ctl c, c
 // ---------------------------------------------------------------------------
 constexpr float kFp32Floor = 2e-6f;
 constexpr int kFp32MaxThreads = 288;  // N + 1 <= 288
+
+// Shared-memory stride of a node record: an odd number of float4 so that the
+// 16-byte reads of consecutive threads fall in different bank groups.
+__host__ __device__ constexpr int fp32_rec_stride(int xs) { return ((xs / 4) % 2 == 0) ? xs + 4 : xs; }
 enum : int { FP32_KEPLER = 0, FP32_CORR = 1 };
 
 __device__ __forceinline__ float encke_F(float q) {
@@ -603,9 +607,11 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
                                                         const float *__restrict__ mu32, const double *__restrict__ Yc,
                                                         double *__restrict__ Yn, const double *__restrict__ E,
                                                         const float *__restrict__ R32, Mix mx) {
-  extern __shared__ float fp32_sm[];
-  float *Gs = fp32_sm;                          // [n][6] force table of the CTA's trajectory
-  float *red = fp32_sm + (size_t)s.n * 6;      // [2][warps] change / size partial maxima
+  extern __shared__ float4 fp32_sm4[];
+  const int xss = fp32_rec_stride(mx.xs);
+  float *Rs = reinterpret_cast<float *>(fp32_sm4);  // [n][xss] node records of the CTA's trajectory
+  float *Gs = Rs + (size_t)s.n * xss;               // [n][6] force table
+  float *red = Gs + (size_t)s.n * 6;                // [2][warps] change / size partial maxima
   const int j = threadIdx.x, lane = j & 31, warp = j >> 5, nw = blockDim.x >> 5;
   const int N = s.N, n = s.n, ld = s.ld, B = md.B, np = 32 * ((N + 32) / 32);
   const bool node = j <= N;
@@ -617,11 +623,17 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int m = list[e];
     const float w2f = (float)c.w2[m];
-    const float4 *rc = reinterpret_cast<const float4 *>(mx.X32 + ((size_t)e * n + (node ? j : 0)) * mx.xs);
+    const float4 *rc = reinterpret_cast<const float4 *>(Rs + (size_t)(node ? j : 0) * xss);
     const size_t yb = (size_t)j * 6 * ld + m;
+    if (MODE == FP32_KEPLER && node) {
+      // the node record written by the set-up kernel, to shared memory
+      const float4 *src = reinterpret_cast<const float4 *>(mx.X32 + ((size_t)e * n + j) * mx.xs);
+      float4 *dst = reinterpret_cast<float4 *>(Rs + (size_t)j * xss);
+      for (int v = 0; v < mx.xs / 4; v++) dst[v] = src[v];
+    }
     if (MODE == FP32_CORR && node) {
       // node record from the FP64 iterate, its residual and the body positions
-      float4 *wc = reinterpret_cast<float4 *>(mx.X32 + ((size_t)e * n + j) * mx.xs);
+      float4 *wc = reinterpret_cast<float4 *>(Rs + (size_t)j * xss);
       double base[6];
       float res[6];
 #pragma unroll
@@ -642,7 +654,6 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
         const float id = rsqrtf(dx * dx + dy * dy + dz * dz);
         wc[4 + b] = make_float4(dx, dy, dz, mu32[b] * id * id * id);
       }
-      __threadfence_block();
     }
     float dl[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acc[6];
     float res[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -697,7 +708,7 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
       for (int q = 0; q < 6; q++) acc[q] = 0.0f;
       if (node) {
         const float *kr = K32T + j;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < n; k++) {
           const float kv = __ldg(kr + (size_t)k * np);
           const float2 *g2 = reinterpret_cast<const float2 *>(Gs + k * 6);
@@ -1096,12 +1107,18 @@ Mix live_mix(const pc_plan *p) {
 
 unsigned sm_ctas(const pc_plan *p, int per_sm) { return (unsigned)((p->num_sms > 0 ? p->num_sms : 152) * per_sm); }
 
+size_t fp32_smem_bytes(const pc_plan *p) {
+  const int threads = 32 * ((p->n + 31) / 32);
+  const int xss = fp32_rec_stride(x32_stride(p->model.B));
+  return sizeof(float) * ((size_t)p->n * (xss + 6) + 2 * (threads / 32));
+}
+
 // FP32 sweeps of one mode over this round's list: CTAs of 32 ceil((N+1)/32) threads.
 template <int MODE>
 void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn, const double *E, const float *R32,
                  const Mix &mx, cudaStream_t st) {
   const int threads = 32 * ((p->n + 31) / 32);
-  const size_t smem = sizeof(float) * ((size_t)p->n * 6 + 2 * (threads / 32));
+  const size_t smem = fp32_smem_bytes(p);
   const Ctl &c = p->ws.ctl[p->ws.live];
   k_fp32<MODE><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), threads, smem, st>>>(s, c, p->model, p->d_K32T, p->d_mu32, Yc,
                                                                            Yn, E, R32, mx);
@@ -1111,8 +1128,11 @@ void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn,
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t prepare_launches(const pc_plan *p) {
-  (void)p;  // the FP32 kernels' shared memory stays under the default limit
-  return cudaSuccess;
+  if (!p->npl) return cudaSuccess;
+  const int bytes = (int)fp32_smem_bytes(p);
+  cudaError_t e = cudaFuncSetAttribute(k_fp32<FP32_KEPLER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fp32<FP32_CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cudaStream_t st) {
