@@ -44,9 +44,10 @@ METRIC = "trajectories/s (N-body, <=1e-10 rel err): mixed+batched vs plain FP64 
 UNIT = "trajectories/s"
 IC_PER_RANK = 4096
 
-# DRAM bytes (read + write) of the FP64 contraction per trajectory-sweep from an
-# ncu capture of the current kernel (profiles/); None until one exists.
-TRAFFIC_BYTES_PER_SWEEP = None
+# DRAM bytes (read + write) of the FP64 contraction per trajectory-sweep, from
+# the ncu capture summarised in profiles/kernels_flyby2048_halfyear_ncu.md
+# (34.6 MB over ~1262 trajectory-sweeps); scaled to a headline launch by its sweeps.
+TRAFFIC_BYTES_PER_SWEEP = 27_422
 
 
 def _peaks():
