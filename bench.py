@@ -17,9 +17,12 @@ copied back inside the timed region.  --impl reference times the CPU oracle
 on a bounded sample of the same workload on the host cores.
 
 The headline path is the mixed-precision batched sweep (FP32 sweeps on the
-deviation from the Keplerian warm start, then FP64 refinement to 1e-13); the
-plain FP64 GPU sweep runs on the same inputs and is reported beside it
-(stats.plain_fp64), with the difference between the two results.
+deviation from the Keplerian warm start, FP64 sweeps with FP32 correction
+solves between them, to 1e-13); the plain FP64 GPU sweep runs on the same
+inputs and is reported beside it (stats.plain_fp64), with the difference
+between the two results.  --workload precision | uneven | adjoint run the
+65,536-trajectory precision study, the 1,048,576-trajectory uneven batch and
+the reverse-mode workload instead, each printing its own line.
 
 With N > 1 (torchrun) each rank propagates its own 4096 trajectories (weak
 scaling, no data-path collective); rank 0 prints the max-over-ranks time.
@@ -370,9 +373,13 @@ def run_ours(args, world, rank, local):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rate, secs = oracle_rate(w, min(M, args.cpu_sample), cores)
+            n1 = min(M, max(1, args.cpu_sample // 16))
+            rate1, secs1 = oracle_rate(w, n1, 1)
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"first {min(M, args.cpu_sample)} trajectories of the workload, full "
-                             f"{args.years:g}-year arcs, {secs:.1f} s on {cores} threads"}
+                             f"{args.years:g}-year arcs, {secs:.1f} s on {cores} threads",
+                   "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                     "sample": f"first {n1} trajectories, {secs1:.1f} s"}}
         stats = {"sweep_rounds_per_step": rounds_total / max(1, args.steps),
                  "trajectory_sweeps_fp64_per_step": sweeps64 / max(1, args.steps),
                  "trajectory_sweeps_fp32_per_step": ktimes["sweeps32"] / max(1, args.steps),

@@ -33,6 +33,6 @@ def test_host_only_entry_points():
     from paper_2301_03989_gb300 import pcprop
     o = pcprop.options_default()
     assert o.tol == 1e-13 and o.max_iters == 60 and o.relative == 1 and o.trunc_tol == 1e-13
-    assert o.precision == pcprop.PC_PREC_FP64 and o.switch_tol == 0.0
+    assert o.precision == pcprop.PC_PREC_FP64 and o.switch_tol == 0.0 and o.refine32 == 1
     assert pcprop.status_string(pcprop.PC_EINVAL) == "invalid argument"
     assert pcprop.lib().pc_options_default(None) == pcprop.PC_EINVAL
