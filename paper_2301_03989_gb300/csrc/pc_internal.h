@@ -164,7 +164,7 @@ struct pc_plan {
   // operator: rows are nodes 1..N (row r <-> node r+1), padded to rows_pad x kpad, zeros outside
   double *d_K = nullptr;
   float *d_K32T = nullptr;   // the operator rounded to FP32 and transposed, [N+1][32 npl]
-  int npl = 0;               // nodes per lane of the FP32 warp kernel, ceil((N+1)/32) (0: no mixed path)
+  int npl = 0;               // ceil((N+1)/32): K32T rows are 32 npl floats long (0: no mixed path)
   double *d_tau = nullptr;   // [n]
   double *h_K = nullptr;     // host copy, (N+1) x (N+1)
   double *h_tau = nullptr;   // [n]

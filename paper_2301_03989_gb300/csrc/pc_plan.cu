@@ -140,7 +140,7 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
     for (int k = 0; k < n; k++) Kd[(size_t)r * p->kpad + k] = p->h_K[(size_t)(r + 1) * n + k];
   cudaError_t e = dalloc(&p->d_K, Kd.size());
   if (e == cudaSuccess) e = cudaMemcpy(p->d_K, Kd.data(), sizeof(double) * Kd.size(), cudaMemcpyHostToDevice);
-  // FP32 operator for the mixed-precision warp kernel: K32T[k][j] = K[j][k]
+  // FP32 operator for the mixed-precision kernels: K32T[k][j] = K[j][k]
   // for output nodes j = 0..N laid out as 32 lanes x npl, zero elsewhere.
   if (N + 1 <= 32 * kMaxNpl) {
     p->npl = (N + 32) / 32;

@@ -1,22 +1,27 @@
 // Device kernels of the batched Picard-Chebyshev sweep and their launchers.
 //
-// One "round" advances every unfinished trajectory by one Picard sweep of its
-// own current segment (Section "Matrix form for vectorized and parallel
+// One "round" advances every unfinished trajectory by one step of its own
+// current segment (Section "Matrix form for vectorized and parallel
 // computation"; Eq. 2):
 //   k_setup      new segments only: node times, ephemeris at the nodes,
 //                Keplerian warm start (Sections "Integration concept",
 //                "Dynamics model"), and for mixed precision the FP32 inputs
-//   k_force      FP64 phase: F = omega2 f(Y, t) (the paper's dynamics kernel)
-//   k_contract   FP64 phase: Y' = 1 x0^T + K F on the FP64 tensor cores
+//   k_fp32       mixed precision, one CTA per trajectory: the FP32 phase of a
+//                new segment (Encke-form deviation from the warm start) or an
+//                FP32 correction solve after an FP64 sweep; the result goes to
+//                the next round's buffer
+//   k_force      FP64 sweep: F = omega2 f(Y, t) (the paper's dynamics kernel)
+//   k_contract   FP64 sweep: Y' = 1 x0^T + K F on the FP64 tensor cores
 //                (DMMA), fused with the per-trajectory change
 //                max_j max(|dr|/|r|, |dv|/|v|) (the paper's errCompute +
 //                maxReduce, Section "CPU-GPU cooperated iteration error
-//                computation", without the host round trip)
-//   k_fp32       mixed precision, new segments: the whole FP32 phase (force
-//                deviation from the warm start in Encke form, its contraction,
-//                the change) for one trajectory per warp, then Y = y_K + delta
-//   k_control    per trajectory: stop / switch / stall / resolution tests,
-//                segment accept / halve / advance (piecewise integration)
+//                computation", without the host round trip) and the residual
+//   k_control    per trajectory: stop / stall / resolution tests, segment
+//                accept / halve / advance (piecewise integration), hand-over
+//                of FP32 results, choice of correction solves
+// In mixed precision k_setup and k_fp32 (new segments, corrections) and
+// k_force and k_contract (this round's FP64 list) touch disjoint trajectories
+// and run on two streams, joined before k_control.
 // State layout: node-major, component-planar Y[j][c][slot] (Section "Dynamics
 // model, array sorting, and CUDA kernel"), leading dimension ld over slots.
 // Active trajectories occupy slots [0, A); finished ones are packed out.
@@ -1187,7 +1192,7 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[4], st);
-  // one warp per block: the control work (resolution tests) spreads over all SMs
+  // one warp per CTA: the control work (resolution tests) spreads over all SMs
   k_control<<<blocks_for(s.A, 32), 32, 0, st>>>(s, c, w.tails, Yn, w.ints);
   if (ev) cudaEventRecord(ev[5], st);
   p->acc_launches += s.mixed ? (s.refine ? 6 : 5) : 4;
