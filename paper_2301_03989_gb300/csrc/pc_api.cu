@@ -86,6 +86,7 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   s.mixed = mixed;
   s.switch_tol = o.switch_tol;
   s.refine = mixed && o.refine32;
+  s.mu_c = p->model.mu_c;
   s.max_corr = 2;
   s.corr_hi = 1e-3;
   s.list[0] = w.lists;

@@ -57,8 +57,10 @@ struct Ctl {
   int *depth, *phase, *status, *sweeps, *seg_sweeps, *nstall, *nseg, *need_setup, *last, *ic;
   unsigned *err32;    // final FP32-phase change of a trajectory whose FP32 phase blew up
   int *ncorr;         // FP32 correction solves in the current segment attempt
+  double *kc;         // [kKeplerConsts][ld] warm-start constants of the segment's start state
 };
-constexpr int kCtlDoubles = 16;  // x[6] + t0, tf, total, sgn, hbase, ta, tb, w1, w2, e_best
+constexpr int kKeplerConsts = 11;
+constexpr int kCtlDoubles = 16 + kKeplerConsts;  // x[6] + t0, tf, total, sgn, hbase, ta, tb, w1, w2, e_best, kc
 constexpr int kCtlInts = 12;     // 10 ints + err32 + ncorr
 
 // Sweep parameters of one call.
@@ -76,6 +78,7 @@ struct Sweep {
   long long io_ld, io_off;
   int segments, seg_mode, max_depth, max_iters, stall_sweeps, relative, warm;
   double tol, stall_factor, div_limit, trunc_tol;
+  double mu_c;               // central GM (warm-start constants)
   int mixed;                 // 1: segments start with FP32 sweeps
   double switch_tol;         // FP32 -> FP64 when the FP32 change is below this
   int refine;                // 1: FP32 correction solves between FP64 sweeps

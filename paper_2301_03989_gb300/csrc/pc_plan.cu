@@ -229,6 +229,7 @@ void carve_ctl(void *block, long long ld, Ctl &t) {
   t.ic = (int *)take(4);
   t.err32 = (unsigned *)take(4);
   t.ncorr = (int *)take(4);
+  t.kc = (double *)take(8 * kKeplerConsts);
 }
 }  // namespace
 

@@ -48,6 +48,91 @@ __device__ __forceinline__ void warp_append(bool flag, int value, int *list, int
 }
 
 // ---------------------------------------------------------------------------
+// Keplerian two-body propagation by dt (warm start).  Kepler's equation in the
+// eccentric-anomaly increment X over dt,
+//   F(X) = X - (e cos E0) sin X + (e sin E0)(1 - cos X) - n dt = 0,
+// with e cos E0 = 1 - r0/a and e sin E0 = r0.v0/sqrt(mu a), is solved by
+// Halley's method (third order: X <- X - 2 F F' / (2 F'^2 - F F'')), kept
+// inside the bracket [n dt - 2, n dt + 2] by bisection, from the first-order
+// root X = n dt a/r0 (clamped into the bracket).  Once a step is below 1e-6
+// the cubic convergence puts the next error below 1e-17 and the iteration
+// stops after applying it.  The Lagrange coefficients then map (r0, v0) to
+// (r, v).  The quantities that depend only on the start state are formed once
+// per segment (kepler_consts, when the segment is scheduled) and shared by all
+// its nodes.  A start state that is not a bound ellipse, or an iteration that
+// does not settle, gives no warm start.
+// ---------------------------------------------------------------------------
+constexpr int kKepConsts = kKeplerConsts;
+// c[0] = 1/a (<= 0: not elliptic), c[1] = a, c[2] = e cos E0, c[3] = e sin E0,
+// c[4] = n, c[5] = (r0.v0/sqrt(mu)) sqrt(a), c[6] = a/r0,
+// c[7] = a (r0.v0)/mu, c[8] = r0 sqrt(a)/sqrt(mu), c[9] = -sqrt(mu) sqrt(a) / r0, c[10] = r0
+__device__ void kepler_consts(double mu, const double x0[6], double c[kKepConsts]) {
+  const double r0 = sqrt(x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2]);
+  const double vv = x0[3] * x0[3] + x0[4] * x0[4] + x0[5] * x0[5];
+  const double rv = x0[0] * x0[3] + x0[1] * x0[4] + x0[2] * x0[5];
+  const double inv_a = 2.0 / r0 - vv / mu;
+  c[0] = inv_a;
+  for (int k = 1; k < kKepConsts; k++) c[k] = 0.0;
+  if (!(inv_a > 0.0)) return;
+  const double a = 1.0 / inv_a;
+  const double sqrt_a = sqrt(a);
+  const double sqrt_mu = sqrt(mu);
+  c[1] = a;
+  c[2] = 1.0 - r0 * inv_a;
+  c[3] = rv / (sqrt_mu * sqrt_a);
+  c[4] = sqrt_mu * inv_a / sqrt_a;  // sqrt(mu / a^3)
+  c[5] = rv / sqrt_mu * sqrt_a;
+  c[6] = a / r0;
+  c[7] = a * rv / mu;
+  c[8] = r0 * sqrt_a / sqrt_mu;
+  c[9] = -sqrt_mu * sqrt_a / r0;
+  c[10] = r0;
+}
+
+__device__ bool kepler_solve(const double c[kKepConsts], const double x0[6], double dt, double out[6]) {
+  if (!(c[0] > 0.0)) return false;
+  const double a = c[1], ecE = c[2], esE = c[3];
+  const double M = c[4] * dt;
+  double lo = M - 2.0, hi = M + 2.0;
+  double X = fmin(fmax(M * c[6], lo + 0.5), hi - 0.5);
+  bool ok = false;
+  for (int it = 0; it < 64; it++) {
+    double sX, cX;
+    sincos(X, &sX, &cX);
+    const double F = X - ecE * sX + esE * (1.0 - cX) - M;
+    if (F > 0.0) hi = X; else lo = X;
+    const double d1 = 1.0 - ecE * cX + esE * sX;
+    const double d2 = ecE * sX + esE * cX;
+    double Xn = X - 2.0 * F * d1 / (2.0 * d1 * d1 - F * d2);
+    const bool halley = Xn > lo && Xn < hi;
+    if (!halley) Xn = 0.5 * (lo + hi);
+    const double step = fabs(Xn - X);
+    X = Xn;
+    if ((halley && step <= 1e-6 * (1.0 + fabs(X))) || step <= 1e-15 * (1.0 + fabs(X))) { ok = true; break; }
+  }
+  if (!ok) return false;
+  double sX, cX;
+  sincos(X, &sX, &cX);
+  const double omc = 1.0 - cX;
+  const double r = a + (c[10] - a) * cX + c[5] * sX;
+  const double f = 1.0 - c[6] * omc;
+  const double g = c[7] * omc + c[8] * sX;
+  const double fd = c[9] / r * sX;
+  const double gd = 1.0 - a / r * omc;
+  for (int q = 0; q < 3; q++) {
+    out[q] = f * x0[q] + g * x0[3 + q];
+    out[3 + q] = fd * x0[q] + gd * x0[3 + q];
+  }
+  return true;
+}
+
+__device__ bool kepler_dt(double mu, const double x0[6], double dt, double out[6]) {
+  double c[kKepConsts];
+  kepler_consts(mu, x0, c);
+  return kepler_solve(c, x0, dt, out);
+}
+
+// ---------------------------------------------------------------------------
 // Segment schedule.  The arc [t0, tf] is measured in units u = hbase / 2^D; a
 // segment at depth d starting at unit p spans 2^(D-d) units and is clipped to
 // end exactly at tf.  Products and sums are rounded one at a time (no fused
@@ -71,6 +156,12 @@ __device__ void schedule(const Sweep &s, Ctl &c, int m, int list_next) {
   }
   c.ta[m] = ta;
   c.tb[m] = tb;
+  if (s.warm) {
+    double x0[6], kc[kKepConsts];
+    for (int q = 0; q < 6; q++) x0[q] = c.x[q * s.ld + m];
+    kepler_consts(s.mu_c, x0, kc);
+    for (int q = 0; q < kKepConsts; q++) c.kc[q * s.ld + m] = kc[q];
+  }
   c.w1[m] = dmul(0.5, dadd(tb, ta));
   c.w2[m] = dmul(0.5, dsub(tb, ta));
   c.last[m] = last;
@@ -154,63 +245,6 @@ __global__ void k_init(Sweep s, Ctl c, Model md, const double *__restrict__ x0, 
   warp_append(to64, m, s.l64[s.list_cur], s.l64_cnt + s.list_cur);
 }
 
-// ---------------------------------------------------------------------------
-// Keplerian two-body propagation by dt (warm start).  Kepler's equation in the
-// eccentric-anomaly increment X over dt,
-//   F(X) = X - (e cos E0) sin X + (e sin E0)(1 - cos X) - n dt = 0,
-// with e cos E0 = 1 - r0/a and e sin E0 = r0.v0/sqrt(mu a), is solved by
-// Halley's method (third order: X <- X - 2 F F' / (2 F'^2 - F F'')), kept
-// inside the bracket [n dt - 2, n dt + 2] by bisection.  Once a step is below
-// 1e-6 the cubic convergence puts the next error below 1e-17 and the iteration
-// stops after applying it.  The Lagrange coefficients then map (r0, v0) to
-// (r, v).  Returns false if the orbit is not a bound ellipse or the iteration
-// does not settle.
-// ---------------------------------------------------------------------------
-__device__ bool kepler_dt(double mu, const double x0[6], double dt, double out[6]) {
-  const double r0 = sqrt(x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2]);
-  const double vv = x0[3] * x0[3] + x0[4] * x0[4] + x0[5] * x0[5];
-  const double rv = x0[0] * x0[3] + x0[1] * x0[4] + x0[2] * x0[5];
-  const double inv_a = 2.0 / r0 - vv / mu;
-  if (!(inv_a > 0.0)) return false;
-  const double a = 1.0 / inv_a;
-  const double sqrt_a = sqrt(a);
-  const double sqrt_mu = sqrt(mu);
-  const double ecE = 1.0 - r0 * inv_a;
-  const double esE = rv / (sqrt_mu * sqrt_a);
-  const double nm = sqrt_mu * inv_a / sqrt_a;  // sqrt(mu / a^3)
-  const double M = nm * dt;
-  double lo = M - 2.0, hi = M + 2.0, X = M;
-  bool ok = false;
-  for (int it = 0; it < 64; it++) {
-    double sX, cX;
-    sincos(X, &sX, &cX);
-    const double F = X - ecE * sX + esE * (1.0 - cX) - M;
-    if (F > 0.0) hi = X; else lo = X;
-    const double d1 = 1.0 - ecE * cX + esE * sX;
-    const double d2 = ecE * sX + esE * cX;
-    double Xn = X - 2.0 * F * d1 / (2.0 * d1 * d1 - F * d2);
-    const bool halley = Xn > lo && Xn < hi;
-    if (!halley) Xn = 0.5 * (lo + hi);
-    const double step = fabs(Xn - X);
-    X = Xn;
-    if ((halley && step <= 1e-6 * (1.0 + fabs(X))) || step <= 1e-15 * (1.0 + fabs(X))) { ok = true; break; }
-  }
-  if (!ok) return false;
-  double sX, cX;
-  sincos(X, &sX, &cX);
-  const double omc = 1.0 - cX;
-  const double r = a + (r0 - a) * cX + rv / sqrt_mu * sqrt_a * sX;
-  const double f = 1.0 - a / r0 * omc;
-  const double g = a * rv / mu * omc + r0 * sqrt_a / sqrt_mu * sX;
-  const double fd = -sqrt_mu * sqrt_a / (r * r0) * sX;
-  const double gd = 1.0 - a / r * omc;
-  for (int q = 0; q < 3; q++) {
-    out[q] = f * x0[q] + g * x0[3 + q];
-    out[3 + q] = fd * x0[q] + gd * x0[3 + q];
-  }
-  return true;
-}
-
 // Indirect (frame) term of body b: the central body's own acceleration
 // mu_b r_b/|r_b|^3, summed over bodies; it depends on the node time only.
 __device__ __forceinline__ void add_indirect(const Model &md, int b, const double r[3], double ind[3]) {
@@ -257,7 +291,11 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     double x0[6], y[6];
     for (int q = 0; q < 6; q++) x0[q] = c.x[q * ld + m];
     bool ok = false;
-    if (j > 0 && s.warm) ok = kepler_dt(md.mu_c, x0, dsub(t, c.ta[m]), y);
+    if (j > 0 && s.warm) {
+      double kc[kKepConsts];
+      for (int q = 0; q < kKepConsts; q++) kc[q] = c.kc[q * ld + m];
+      ok = kepler_solve(kc, x0, dsub(t, c.ta[m]), y);
+    }
     if (!ok)
       for (int q = 0; q < 6; q++) y[q] = x0[q];
     float *rec = s.mixed ? mx.X32 + ((size_t)e * s.n + j) * mx.xs : nullptr;
@@ -1024,6 +1062,7 @@ __global__ void k_repack_ctl(Sweep s, Ctl a, Ctl b, const int *__restrict__ pos)
     b.w1[d] = a.w1[m];
     b.w2[d] = a.w2[m];
     b.e_best[d] = a.e_best[m];
+    for (int q = 0; q < kKepConsts; q++) b.kc[q * ld + d] = a.kc[q * ld + m];
     b.err[d] = a.err[m];
     b.p[d] = a.p[m];
     b.depth[d] = a.depth[m];
