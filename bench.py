@@ -276,8 +276,12 @@ def run_ours(args, world, rank, local):
     w = wall.subset(np.arange(lo, hi))
     M = w.n_ic
     mixed = args.precision == "mixed"
+    torch.cuda.synchronize(dev)
+    t_plan = time.perf_counter()
     plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED if mixed else pc.PC_PREC_FP64,
                                  switch_tol=args.switch_tol)
+    torch.cuda.synchronize(dev)
+    plan_ms = 1000.0 * (time.perf_counter() - t_plan)   # operator build + uploads, reported apart
     stream = torch.cuda.Stream(device=dev)
     x0 = torch.as_tensor(W.to_planar(w.x0), device=dev)
     xf = torch.zeros_like(x0)
@@ -385,7 +389,8 @@ def run_ours(args, world, rank, local):
                  "trajectory_sweeps_fp32_per_step": ktimes["sweeps32"] / max(1, args.steps),
                  "status_nonzero": int((status != 0).sum()),
                  "kernel_ms_per_step": {k: ktimes[k][1] / args.steps for k in names},
-                 "instrumented_ms_per_step": sum(prof_ms) / len(prof_ms)}
+                 "instrumented_ms_per_step": sum(prof_ms) / len(prof_ms),
+                 "plan_create_ms": plan_ms}
         if plain is not None:
             stats["plain_fp64"] = {
                 "value": total_ic / (plain["ms"] / 1000.0), "unit": UNIT, "ms_per_step": plain["ms"],
