@@ -390,7 +390,8 @@ def run_ours(args, world, rank, local):
                  "status_nonzero": int((status != 0).sum()),
                  "kernel_ms_per_step": {k: ktimes[k][1] / args.steps for k in names},
                  "instrumented_ms_per_step": sum(prof_ms) / len(prof_ms),
-                 "plan_create_ms": plan_ms}
+                 "plan_create_ms": plan_ms,
+                 "ms_per_step_median": statistics.median(step_ms)}
         if plain is not None:
             stats["plain_fp64"] = {
                 "value": total_ic / (plain["ms"] / 1000.0), "unit": UNIT, "ms_per_step": plain["ms"],
