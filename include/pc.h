@@ -27,9 +27,15 @@
  * Errors: every entry point returns a pc_status; nothing aborts, prints or
  * traps.  Per-trajectory outcomes go to the optional status[] array.
  *
- * Streams: work is issued on the CUDA stream passed in (NULL = legacy default
- * stream).  Use one plan per concurrently used stream: a plan's workspace is
- * shared by all its calls.
+ * Streams: work is ordered on the CUDA stream passed in (NULL = legacy default
+ * stream): it starts after the stream's earlier work and the stream's later
+ * work waits for it.  A propagation called on a default stream (legacy or
+ * per-thread) runs on a stream the plan owns, forked from and joined back to
+ * the caller's by events, because a default stream cannot be captured into
+ * the CUDA graphs the round loop replays.  In mixed precision each round also
+ * uses a second stream of the plan for its new-segment branch.  Use one plan
+ * per concurrently used stream: a plan's workspace and streams are shared by
+ * all its calls.
  */
 #ifndef PC_H_
 #define PC_H_
