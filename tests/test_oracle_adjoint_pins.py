@@ -263,3 +263,24 @@ def test_stm_composition(ora):
     x1, P1, _, _ = ora.stm_propagate(m, o, x0, bounds[: k + 1])
     _, P2, _, _ = ora.stm_propagate(m, o, x1, bounds[k:])
     assert _scaled_rel(P2 @ P1, P_all, H6) < 1e-11
+
+
+def test_gl_stm_matches_gl_finite_differences(ora):
+    """Gauss-Legendre variational integration against central differences of
+    the 6-state Gauss-Legendre integrator (same steps; 10 km / 1e-5 km/s)."""
+    w = W.config1(M=1)
+    m, o = _model(ora, w), _opts(ora, w)
+    x0 = w.x0[0]
+    steps = 600
+    _, P, capped = ora.gl_stm_propagate(m, x0, w.t0, w.tf, steps)
+    assert capped == 0
+    h = 10.0 * H6
+    fd = np.zeros((6, 6))
+    for q in range(6):
+        e = np.zeros(6)
+        e[q] = h[q]
+        xp, c1 = ora.gl_propagate(m, o, x0 + e, w.t0, w.tf, steps)
+        xm, c2 = ora.gl_propagate(m, o, x0 - e, w.t0, w.tf, steps)
+        assert c1 == c2 == 0
+        fd[:, q] = (xp - xm) / (2 * h[q])
+    assert _scaled_rel(P, fd, h) < 3e-8
