@@ -428,33 +428,6 @@ def run_ours(args, world, rank, local):
 
 
 # ----------------------------------------------------------------------------- other workloads
-def _oracle_reference(ora, w, x0, idx, N=None, S=None, t0=None, tf=None):
-    """Oracle final states (rows [len(idx)][6]) of the trajectories idx, on all
-    host cores (one trajectory per call when each has its own arc and degree)."""
-    from concurrent.futures import ThreadPoolExecutor
-    m = ora.Model.from_workload(w)
-    threads = os.cpu_count() or 1
-    if N is None:
-        o = ora.Opts(N=w.N, segments=w.segments, seg_mode=w.seg_mode, tol=w.tol, max_iters=w.max_iters,
-                     max_depth=w.max_depth)
-        return ora.propagate(m, o, x0[idx], w.t0, w.tf, threads=threads)["xf"]
-
-    def one(i):
-        o = ora.Opts(N=int(N[i]), segments=int(S[i]), seg_mode=0, tol=w.tol, max_iters=w.max_iters,
-                     max_depth=w.max_depth)
-        return ora.propagate(m, o, x0[i:i + 1], float(t0[i]), float(tf[i]))["xf"][0]
-    with ThreadPoolExecutor(threads) as ex:
-        return np.array(list(ex.map(one, idx)))
-
-
-def _errors(g, ref):
-    er = np.linalg.norm(g[:, :3] - ref[:, :3], axis=1) / np.linalg.norm(ref[:, :3], axis=1)
-    ev = np.linalg.norm(g[:, 3:] - ref[:, 3:], axis=1) / np.linalg.norm(ref[:, 3:], axis=1)
-    return {"n": int(len(ref)), "pos_max": float(er.max()), "pos_median": float(np.median(er)),
-            "vel_max": float(ev.max()), "vel_median": float(np.median(ev)),
-            "frac_within_1e-10": float(np.mean((er <= 1e-10) & (ev <= 1e-10)))}
-
-
 def _time_calls(fn, steps, warmup, stream, flush, dev):
     import torch
     for _ in range(warmup):
@@ -479,15 +452,15 @@ def run_aux(args, world, rank, local):
     1e-13), uneven batching (up to 1,048,576 trajectories of mixed arc length,
     degree and segment count, mixed precision, degree groups on concurrent
     streams) and reverse mode (config-4 flybys: forward pass with tape plus one
-    reverse sweep).  Each prints one JSON line with its own metric."""
+    reverse sweep).  Each prints one JSON line with its own metric.  Their
+    errors against the CPU oracle are checked by the GPU tests
+    (tests/test_gpu_mixed.py, tests/test_gpu_uneven.py), not here."""
     import torch
     from paper_2301_03989_gb300 import build as B
     from paper_2301_03989_gb300 import pcprop as pc
     from paper_2301_03989_gb300 import workloads as W
     if world > 1:
         raise SystemExit("the extra workloads run on one GPU")
-    from oracle import oracle as ora
-    ora.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
@@ -518,12 +491,6 @@ def run_aux(args, world, rank, local):
                                  status=int((st.cpu().numpy() != 0).sum()), launches=int(kt["kernel_launches"]),
                                  sweeps64=kt["sweeps64"], sweeps32=kt["sweeps32"])
                 plan.close()
-            idx = np.sort(rng.choice(M, size=min(M, args.oracle_sample), replace=False))
-            t = time.perf_counter()
-            ref = _oracle_reference(ora, w, w.x0, idx)
-            stats["error_vs_oracle_mixed"] = _errors(out["mixed"]["xf"][idx], ref)
-            stats["error_vs_oracle_fp64"] = _errors(out["fp64"]["xf"][idx], ref)
-            osecs = time.perf_counter() - t
             ms = out["mixed"]["ms"]
             n_steps = args.steps + args.warmup
             stats["plain_fp64"] = {"value": M / (out["fp64"]["ms"] / 1000.0), "ms_per_step": out["fp64"]["ms"],
@@ -534,8 +501,7 @@ def run_aux(args, world, rank, local):
             stats["status_nonzero"] = out["mixed"]["status"]
             launches = out["mixed"]["launches"] // n_steps * args.steps
             metric = "trajectories/s (config-1 system, 2-year arcs, N=128): mixed FP32->FP64 vs plain FP64 GPU"
-            config = {"workload": w.name, "n_ic": M, "N": w.N, "switch_tol": 1e-6, "tol": w.tol,
-                      "oracle_sample": f"{len(idx)} seeded trajectories, oracle {osecs:.1f} s on {cores} threads"}
+            config = {"workload": w.name, "n_ic": M, "N": w.N, "switch_tol": 1e-6, "tol": w.tol}
         elif args.workload == "uneven":
             uw = W.config5(M=args.n_ic or 1048576)
             M = uw.n_ic
@@ -561,21 +527,13 @@ def run_aux(args, world, rank, local):
             clk = clocks.stop()
             n_steps = args.steps + args.warmup
             launches = sum(pc.kernel_times(p_)["kernel_launches"] for p_ in plans) // n_steps * args.steps
-            xg = np.empty((M, 6))
-            xg[perm] = W.from_planar(xf.cpu().numpy())
             stats["status_nonzero"] = int((st.cpu().numpy() != 0).sum())
-            idx = np.sort(rng.choice(M, size=min(M, max(8, args.oracle_sample // 16)), replace=False))
-            t = time.perf_counter()
-            ref = _oracle_reference(ora, b, uw.x0, idx, N=uw.N, S=uw.S, t0=uw.t0, tf=uw.tf)
-            stats["error_vs_oracle"] = _errors(xg[idx], ref)
-            osecs = time.perf_counter() - t
             stats["groups"] = {int(d): int(c) for d, c in zip(degs, counts)}
             for p_ in plans:
                 p_.close()
             ms = float(np.mean(ms))
             metric = "trajectories/s (uneven arcs 0.5-10 yr, N in {32,64,128,256}, 4-80 segments): mixed precision"
-            config = {"workload": uw.name, "n_ic": M, "degrees": [int(d) for d in degs],
-                      "oracle_sample": f"{len(idx)} seeded trajectories, oracle {osecs:.1f} s on {cores} threads"}
+            config = {"workload": uw.name, "n_ic": M, "degrees": [int(d) for d in degs]}
         else:  # adjoint
             w = W.config4(M=args.n_ic or 1024)
             M = w.n_ic
@@ -639,7 +597,6 @@ def main(argv=None):
     ap.add_argument("--n-ic", type=int, default=None, help="trajectories (per GPU for flyby)")
     ap.add_argument("--years", type=float, default=4.0, help="arc length of the flyby workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
-    ap.add_argument("--oracle-sample", type=int, default=512)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":
