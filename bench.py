@@ -508,9 +508,10 @@ def run_aux(args, world, rank, local):
             perm, degs, counts = uw.groups()
             plans = []
             b = uw.base
+            prec = pc.PC_PREC_FP64 if args.precision == "fp64" else pc.PC_PREC_MIXED
             for d in degs:
                 o = pc.options_default(tol=b.tol, max_iters=b.max_iters, max_depth=b.max_depth, seg_mode=0,
-                                       precision=pc.PC_PREC_MIXED)
+                                       precision=prec)
                 plans.append(pc.plan_create(int(d), 4, b.mu_central, b.mu, b.t_begin, b.granule, b.coef,
                                             b.indirect, o))
             x0 = torch.as_tensor(W.to_planar(uw.x0[perm]), device=dev)
@@ -532,8 +533,9 @@ def run_aux(args, world, rank, local):
             for p_ in plans:
                 p_.close()
             ms = float(np.mean(ms))
-            metric = "trajectories/s (uneven arcs 0.5-10 yr, N in {32,64,128,256}, 4-80 segments): mixed precision"
-            config = {"workload": uw.name, "n_ic": M, "degrees": [int(d) for d in degs]}
+            metric = ("trajectories/s (uneven arcs 0.5-10 yr, N in {32,64,128,256}, 4-80 segments): "
+                      + ("plain FP64" if args.precision == "fp64" else "mixed precision"))
+            config = {"workload": uw.name, "n_ic": M, "degrees": [int(d) for d in degs], "precision": args.precision}
         else:  # adjoint
             w = W.config4(M=args.n_ic or 1024)
             M = w.n_ic
