@@ -101,6 +101,9 @@ def lib():
             L.ora_gl_stm_propagate.restype = C.c_int
             L.ora_bplane.argtypes = [C.c_double, P(C.c_double), P(C.c_double)]
             L.ora_bplane.restype = C.c_int
+            L.ora_pc2_segment.argtypes = [P(_Model), P(_Opts), C.c_double, C.c_double, P(C.c_double),
+                                          P(C.c_double), P(C.c_int), P(C.c_double)]
+            L.ora_pc2_segment.restype = C.c_int
             _lib = L
     return _lib
 
@@ -324,3 +327,16 @@ def bplane(mu: float, rel) -> tuple[np.ndarray, int]:
     out = np.zeros(2)
     rc = lib().ora_bplane(float(mu), _dp(rel), _dp(out))
     return out, int(rc)
+
+
+def pc2_segment(model: Model, opts: Opts, ta: float, tb: float, x0):
+    """Second-order form of the sweep (velocities from the accelerations, then
+    positions from the new velocities): (Y [n][6], sweeps, last change, outcome)."""
+    s, o = model.struct(), opts.struct()
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    Y = np.zeros((opts.N + 1, 6))
+    it = C.c_int(0)
+    err = C.c_double(0.0)
+    outcome = lib().ora_pc2_segment(C.byref(s), C.byref(o), float(ta), float(tb), _dp(x0), _dp(Y), C.byref(it),
+                                    C.byref(err))
+    return Y, int(it.value), float(err.value), int(outcome)

@@ -36,6 +36,9 @@
  *   ora_gl_stm_propagate pinned: finite differences of ora_gl_propagate
  *   ora_bplane           pinned: straight-line limit, hyperbola built from a
  *                                chosen asymptote and aim point
+ *   ora_pc2_segment      pinned: constant acceleration exact, harmonic
+ *                                oscillator closed form, same fixed point as
+ *                                ora_pc_segment on a flyby-free segment
  */
 #include <math.h>
 #include <pthread.h>
@@ -1020,4 +1023,91 @@ int ora_bplane(double mu, const double rel[6], double out[2]) {
   out[0] = Bv[0] * T[0] + Bv[1] * T[1] + Bv[2] * T[2];
   out[1] = Bv[0] * R[0] + Bv[1] * R[1] + Bv[2] * R[2];
   return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Second-order form of the Picard iteration (groundwork for the        */
+/* second-order PC the paper names as a further gain, after Junkins et   */
+/* al. 2013; not used by the CUDA library).  For r'' = a(r, v, t) the    */
+/* velocity nodes come from the integral of the acceleration interpolant */
+/* and the position nodes from the integral of the interpolant of those  */
+/* new velocities, with the same operator K:                             */
+/*   V' = v0 + omega2 K A(R, V),   R' = r0 + omega2 K V'.                 */
+/* Same node times, warm start, stopping rule (the state change of       */
+/* ora_pc_segment_core), stall rule and cap; no resolution test.         */
+/* Returns the outcome (ORA_SEG_*); Y [n][6] holds the last iterate.     */
+/* ------------------------------------------------------------------ */
+int ora_pc2_segment(const ora_model *m, const ora_opts *o, double ta, double tb, const double x0[6], double *Y,
+                    int *iters, double *err) {
+  const int N = o->N, n = N + 1, B = (o->dyn == ORA_DYN_NBODY) ? m->n_bodies : 0;
+  double *K = (double *)malloc(sizeof(double) * n * n);
+  double *tau = (double *)malloc(sizeof(double) * n);
+  double *A = (double *)malloc(sizeof(double) * 3 * n);
+  double *Yn = (double *)malloc(sizeof(double) * 6 * n);
+  double *eph = (double *)malloc(sizeof(double) * (size_t)n * (B > 0 ? B : 1) * 3);
+  ora_pc_operator(N, o->truncated, K);
+  ora_cgl_nodes(N, tau);
+  const double w1 = 0.5 * (tb + ta), w2 = 0.5 * (tb - ta);
+  for (int j = 0; j < n; j++) {
+    const double t = w1 + w2 * tau[j];
+    if (B > 0) ora_ephem_eval(m, t, eph + (size_t)j * B * 3);
+    int bad = 1;
+    if (o->warm_start && o->dyn == ORA_DYN_NBODY) bad = ora_kepler(m->mu_central, x0, t - ta, Y + 6 * j);
+    if (bad)
+      for (int c = 0; c < 6; c++) Y[6 * j + c] = x0[c];
+  }
+  for (int c = 0; c < 6; c++) Y[c] = x0[c];
+  double e_best = INFINITY, e = INFINITY;
+  int nstall = 0, outcome = ORA_SEG_FAIL_CAP, i;
+  for (i = 1; i <= o->max_iters; i++) {
+    for (int j = 0; j < n; j++) {
+      double f[6];
+      ora_f(m, o, B ? eph + (size_t)j * B * 3 : NULL, Y + 6 * j, f);
+      for (int c = 0; c < 3; c++) A[3 * j + c] = f[3 + c];
+    }
+    for (int j = 0; j < n; j++)      /* velocities from the accelerations */
+      for (int c = 0; c < 3; c++) {
+        double s = 0.0;
+        for (int k = 0; k < n; k++) s += K[j * n + k] * A[3 * k + c];
+        Yn[6 * j + 3 + c] = x0[3 + c] + w2 * s;
+      }
+    for (int j = 0; j < n; j++)      /* positions from the new velocities */
+      for (int c = 0; c < 3; c++) {
+        double s = 0.0;
+        for (int k = 0; k < n; k++) s += K[j * n + k] * Yn[6 * k + 3 + c];
+        Yn[6 * j + c] = x0[c] + w2 * s;
+      }
+    e = 0.0;
+    for (int j = 0; j < n; j++) {
+      const double *yn = Yn + 6 * j, *yo = Y + 6 * j;
+      double dr = sqrt((yn[0] - yo[0]) * (yn[0] - yo[0]) + (yn[1] - yo[1]) * (yn[1] - yo[1]) +
+                       (yn[2] - yo[2]) * (yn[2] - yo[2]));
+      double dv = sqrt((yn[3] - yo[3]) * (yn[3] - yo[3]) + (yn[4] - yo[4]) * (yn[4] - yo[4]) +
+                       (yn[5] - yo[5]) * (yn[5] - yo[5]));
+      if (o->relative) {
+        double nr = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+        double nv = sqrt(yn[3] * yn[3] + yn[4] * yn[4] + yn[5] * yn[5]);
+        if (nr > 0.0) dr = dr / nr;
+        if (nv > 0.0) dv = dv / nv;
+      }
+      double ej = dr > dv ? dr : dv;
+      if (!(ej <= e)) e = ej;
+    }
+    memcpy(Y, Yn, sizeof(double) * 6 * n);
+    int out = -1;
+    if (!(e <= o->div_limit)) {
+      out = ORA_SEG_FAIL_DIV;
+    } else if (e < o->tol) {
+      out = ORA_SEG_OK;
+    } else {
+      if (e < e_best) { e_best = e; nstall = 0; } else { nstall++; }
+      if (nstall >= o->stall_sweeps && e_best < o->stall_factor * o->tol) out = ORA_SEG_STALLED;
+    }
+    if (out >= 0) { outcome = out; break; }
+  }
+  if (i > o->max_iters) i = o->max_iters;
+  if (iters) *iters = i;
+  if (err) *err = e;
+  free(K); free(tau); free(A); free(Yn); free(eph);
+  return outcome;
 }
