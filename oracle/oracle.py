@@ -58,6 +58,10 @@ class _Opts(C.Structure):
                 ("dyn_param", C.c_double * 3)]
 
 
+class _StopState(C.Structure):
+    _fields_ = [("e_best", C.c_double), ("nstall", C.c_int)]
+
+
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -104,6 +108,11 @@ def lib():
             L.ora_pc2_segment.argtypes = [P(_Model), P(_Opts), C.c_double, C.c_double, P(C.c_double),
                                           P(C.c_double), P(C.c_int), P(C.c_double)]
             L.ora_pc2_segment.restype = C.c_int
+            L.ora_stop_rule.argtypes = [P(_Opts), P(_StopState), C.c_double, C.c_int]
+            L.ora_stop_rule.restype = C.c_int
+            L.ora_propagate_log.argtypes = [P(_Model), P(_Opts), P(C.c_double), C.c_double, C.c_double,
+                                            P(C.c_double), P(C.c_int), P(C.c_int), P(C.c_int), C.c_int,
+                                            P(C.c_double), P(C.c_int)]
             _lib = L
     return _lib
 
@@ -248,6 +257,34 @@ def propagate(model: Model, opts: Opts, x0, t0: float, tf: float, threads: int =
     if ck is not None:
         out["ckpt"] = ck
     return out
+
+
+def stop_rule(opts: Opts, changes) -> tuple[int, int]:
+    """Feeds the sweep changes one by one to the oracle's stop rule; returns
+    (outcome, sweep) at the first sweep that ends the attempt, or (-1, len)
+    if none does."""
+    o = opts.struct()
+    st = _StopState(float("inf"), 0)
+    for i, e in enumerate(changes, start=1):
+        out = lib().ora_stop_rule(C.byref(o), C.byref(st), float(e), i)
+        if out >= 0:
+            return int(out), i
+    return -1, len(changes)
+
+
+def propagate_log(model: Model, opts: Opts, x0, t0: float, tf: float, max_log: int = 256) -> dict:
+    """One trajectory with its segment-attempt log: log [k] = (t_a, t_b,
+    outcome, sweeps, depth) of each attempt in order."""
+    s, o = model.struct(), opts.struct()
+    x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64).reshape(6))
+    xf = np.zeros(6)
+    status, iters, nseg, nlog = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
+    log = np.zeros((max_log, 5))
+    lib().ora_propagate_log(C.byref(s), C.byref(o), _dp(x0), float(t0), float(tf), _dp(xf), C.byref(status),
+                            C.byref(iters), C.byref(nseg), int(max_log), _dp(log), C.byref(nlog))
+    k = min(int(nlog.value), max_log)
+    return dict(xf=xf, status=int(status.value), iters=int(iters.value), nseg=int(nseg.value),
+                n_attempts=int(nlog.value), log=log[:k])
 
 
 def tail_estimate(opts: Opts, G, Y, w2: float) -> float:

@@ -19,6 +19,10 @@
  *   ora_pc_operator      pinned: exact on polynomials, Clenshaw-Curtis weights
  *   ora_ephem_eval       pinned: numpy chebval, interpolation at fit nodes,
  *                                 the later granule on a boundary
+ *   ora_stop_rule        pinned: hand-derived outcomes of written-out
+ *                                change sequences (tol, stall, cap, blow-up)
+ *   ora_propagate_log    pinned: hand-derived attempt sequences (halve,
+ *                                accept, grow back, clip at tf, backward)
  *   ora_accel            pinned: finite-difference gradient of the potential,
  *                                collinear closed form, Kepler conservation
  *   ora_kepler           pinned: Kepler's-equation residual, energy/momentum,
@@ -182,16 +186,16 @@ void ora_pc_operator(int N, int truncated, double *K) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Ephemeris: the table's Chebyshev series written out,                 */
-/*   r_b = sum_{k=0}^{deg} c_k T_k(sigma),                               */
-/* with T_0 = 1, T_1 = sigma, T_{k+1} = 2 sigma T_k - T_{k-1}, and the   */
-/* sum taken from the highest degree down, one fused multiply-add (one  */
-/* rounding, C99 fma) per recurrence step and per term.  The paper      */
-/* evaluates planetary states once at the fixed node times before the   */
-/* iterations (Section "Dynamics model, array sorting, and CUDA kernel")*/
-/* and does not fix how the tables are summed.  A time exactly on a     */
-/* granule boundary uses the later granule; times outside the table use */
-/* the nearest granule.  Degrees above 63 are not supported (zeros).    */
+/* Ephemeris: Clenshaw evaluation of the table's Chebyshev series      */
+/*   r_b = sum_{k=0}^{deg} c_k T_k(sigma)                                */
+/* by the backward recurrence b_k = c_k + 2 sigma b_{k+1} - b_{k+2},     */
+/* r_b = c_0 + sigma b_1 - b_2 (Clenshaw 1955), each operation rounded  */
+/* on its own.  The paper evaluates planetary states once at the fixed  */
+/* node times before the iterations (Section "Dynamics model, array     */
+/* sorting, and CUDA kernel") and does not fix how the tables are       */
+/* summed; Clenshaw's recurrence is the textbook evaluation of a        */
+/* Chebyshev series.  A time exactly on a granule boundary uses the     */
+/* later granule; times outside the table use the nearest granule.      */
 /* ------------------------------------------------------------------ */
 void ora_ephem_eval(const ora_model *m, double t, double *rb /* [n_bodies][3] */) {
   const int nc = m->degree + 1;
@@ -200,19 +204,16 @@ void ora_ephem_eval(const ora_model *m, double t, double *rb /* [n_bodies][3] */
   if (g > m->n_granules - 1) g = m->n_granules - 1;
   const double tg = m->t_begin + (double)g * m->granule;
   const double sigma = 2.0 * (t - tg) / m->granule - 1.0;
-  double T[64];
-  for (int b = 0; b < m->n_bodies; b++)
-    for (int ax = 0; ax < 3; ax++) rb[b * 3 + ax] = 0.0;
-  if (nc > 64) return;
-  T[0] = 1.0;
-  if (nc > 1) T[1] = sigma;
-  for (int k = 2; k < nc; k++) T[k] = fma(2.0 * sigma, T[k - 1], -T[k - 2]);
   for (int b = 0; b < m->n_bodies; b++) {
     for (int ax = 0; ax < 3; ax++) {
       const double *c = m->coef + (((size_t)b * m->n_granules + g) * 3 + ax) * nc;
-      double acc = 0.0;
-      for (int k = nc - 1; k >= 0; k--) acc = fma(c[k], T[k], acc);
-      rb[b * 3 + ax] = acc;
+      double b1 = 0.0, b2 = 0.0;
+      for (int k = nc - 1; k >= 1; k--) {
+        double b0 = c[k] + 2.0 * sigma * b1 - b2;
+        b2 = b1;
+        b1 = b0;
+      }
+      rb[b * 3 + ax] = c[0] + sigma * b1 - b2;
     }
   }
 }
@@ -389,6 +390,39 @@ double ora_tail_estimate(const ora_opts *o, const double *G, const double *Y, do
 }
 
 /* ------------------------------------------------------------------ */
+/* Stop rule of a segment attempt, applied after sweep `sweep` (1-based) */
+/* with change e.  The paper stops when the change drops below the      */
+/* tolerance (Section "Matrix form", stopping criterion); it leaves the */
+/* cap and stagnation unstated, so this restatement adds, in this order:*/
+/*   e non-finite or above div_limit   -> ORA_SEG_FAIL_DIV              */
+/*   e < tol (strict)                  -> ORA_SEG_OK                    */
+/*   e not below the best change so far for stall_sweeps sweeps in a    */
+/*   row while that best is below stall_factor * tol -> ORA_SEG_STALLED */
+/*   sweep == max_iters                -> ORA_SEG_FAIL_CAP              */
+/*   otherwise -1 (sweep again).                                        */
+/* A change equal to the best counts as no improvement.  st carries the */
+/* best change and the count between calls; start it at {INFINITY, 0}.  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  double e_best;
+  int nstall;
+} ora_stop_state;
+
+int ora_stop_rule(const ora_opts *o, ora_stop_state *st, double e, int sweep) {
+  if (!(e <= o->div_limit)) return ORA_SEG_FAIL_DIV;
+  if (e < o->tol) return ORA_SEG_OK;
+  if (e < st->e_best) {
+    st->e_best = e;
+    st->nstall = 0;
+  } else {
+    st->nstall++;
+  }
+  if (st->nstall >= o->stall_sweeps && st->e_best < o->stall_factor * o->tol) return ORA_SEG_STALLED;
+  if (sweep >= o->max_iters) return ORA_SEG_FAIL_CAP;
+  return -1;
+}
+
+/* ------------------------------------------------------------------ */
 /* One PC segment for one trajectory: the Picard iteration of Eq. (2) in */
 /* the matrix form of the paper with the operator K built above.        */
 /*   t_j = omega1 + omega2 tau_j, omega1 = (tb+ta)/2, omega2 = (tb-ta)/2 */
@@ -422,8 +456,9 @@ static int ora_pc_segment_core(const ora_model *m, const ora_opts *o, const doub
       for (int c = 0; c < 6; c++) Y[6 * j + c] = x0[c];
   }
   for (int c = 0; c < 6; c++) Y[c] = x0[c];
-  double e_best = INFINITY, e = INFINITY;
-  int nstall = 0, outcome = ORA_SEG_FAIL_CAP, i;
+  double e = INFINITY;
+  ora_stop_state st = {INFINITY, 0};
+  int outcome = ORA_SEG_FAIL_CAP, i;
   for (i = 1; i <= o->max_iters; i++) {
     for (int j = 0; j < n; j++) ora_f(m, o, B ? ephem + (size_t)j * B * 3 : NULL, Y + 6 * j, G + 6 * j);
     for (int j = 0; j < n; j++) {
@@ -449,15 +484,7 @@ static int ora_pc_segment_core(const ora_model *m, const ora_opts *o, const doub
       double ej = dr > dv ? dr : dv;
       if (!(ej <= e)) e = ej; /* propagates NaN */
     }
-    int out = -1;
-    if (!(e <= o->div_limit)) {
-      out = ORA_SEG_FAIL_DIV;
-    } else if (e < o->tol) {
-      out = ORA_SEG_OK;
-    } else {
-      if (e < e_best) { e_best = e; nstall = 0; } else { nstall++; }
-      if (nstall >= o->stall_sweeps && e_best < o->stall_factor * o->tol) out = ORA_SEG_STALLED;
-    }
+    int out = ora_stop_rule(o, &st, e, i);
     /* resolution test on an accepted segment: the force table of this sweep
        against the norms of the iterate it was evaluated on (Y, not yet updated) */
     if ((out == ORA_SEG_OK || out == ORA_SEG_STALLED) && o->trunc_tol > 0.0 &&
@@ -511,6 +538,9 @@ typedef struct {
   int *status, *iters, *nseg;
   int max_ckpt;
   double *ckpt;
+  int max_log;         /* attempt log of one trajectory (tests), or 0 */
+  double *log;         /* [max_log][5] = (ta, tb, outcome, sweeps, depth) */
+  int *n_log;          /* attempts made (may exceed max_log) */
   long begin, end;
 } ora_job;
 
@@ -561,6 +591,13 @@ static void ora_one_ic(const ora_job *J, long ic) {
     double err = 0.0;
     int r = ora_pc_segment_core(m, o, J->K, J->tau, ta, tb, x, Y, G, Yn, tj, eph, &it, &err);
     sweeps += it;
+    if (J->n_log) {
+      if (*J->n_log < J->max_log) {
+        double *lg = J->log + (size_t)(*J->n_log) * 5;
+        lg[0] = ta; lg[1] = tb; lg[2] = (double)r; lg[3] = (double)it; lg[4] = (double)depth;
+      }
+      (*J->n_log)++;
+    }
     int accept = (r == ORA_SEG_OK || r == ORA_SEG_STALLED);
     if (r == ORA_SEG_FAIL_TRUNC && depth >= D) { accept = 1; status |= ORA_IC_UNRESOLVED; }
     if (accept) {
@@ -618,6 +655,27 @@ void ora_propagate(const ora_model *m, const ora_opts *o, long n_ic, const doubl
     for (int w = 0; w < n_threads; w++) pthread_join(th[w], NULL);
   }
   free(jobs); free(th); free(K); free(tau);
+}
+
+/* One trajectory with its attempt log (tests of the segment schedule): */
+/* log[k] = (t_a, t_b, outcome ORA_SEG_*, sweeps, depth) of the k-th     */
+/* segment attempt, for k < max_log; *n_log = attempts made.  Same       */
+/* schedule and results as ora_propagate.                                */
+void ora_propagate_log(const ora_model *m, const ora_opts *o, const double x0[6], double t0, double tf, double xf[6],
+                       int *status, int *iters, int *nseg, int max_log, double *log, int *n_log) {
+  const int n = o->N + 1;
+  double *K = (double *)malloc(sizeof(double) * n * n);
+  double *tau = (double *)malloc(sizeof(double) * n);
+  ora_pc_operator(o->N, o->truncated, K);
+  ora_cgl_nodes(o->N, tau);
+  ora_job J;
+  memset(&J, 0, sizeof(J));
+  J.m = m; J.o = o; J.K = K; J.tau = tau; J.t0 = t0; J.tf = tf; J.x0 = x0; J.xf = xf;
+  J.status = status; J.iters = iters; J.nseg = nseg;
+  J.max_log = max_log; J.log = log; J.n_log = n_log;
+  *n_log = 0;
+  ora_one_ic(&J, 0);
+  free(K); free(tau);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1057,8 +1115,9 @@ int ora_pc2_segment(const ora_model *m, const ora_opts *o, double ta, double tb,
       for (int c = 0; c < 6; c++) Y[6 * j + c] = x0[c];
   }
   for (int c = 0; c < 6; c++) Y[c] = x0[c];
-  double e_best = INFINITY, e = INFINITY;
-  int nstall = 0, outcome = ORA_SEG_FAIL_CAP, i;
+  double e = INFINITY;
+  ora_stop_state st = {INFINITY, 0};
+  int outcome = ORA_SEG_FAIL_CAP, i;
   for (i = 1; i <= o->max_iters; i++) {
     for (int j = 0; j < n; j++) {
       double f[6];
@@ -1094,15 +1153,7 @@ int ora_pc2_segment(const ora_model *m, const ora_opts *o, double ta, double tb,
       if (!(ej <= e)) e = ej;
     }
     memcpy(Y, Yn, sizeof(double) * 6 * n);
-    int out = -1;
-    if (!(e <= o->div_limit)) {
-      out = ORA_SEG_FAIL_DIV;
-    } else if (e < o->tol) {
-      out = ORA_SEG_OK;
-    } else {
-      if (e < e_best) { e_best = e; nstall = 0; } else { nstall++; }
-      if (nstall >= o->stall_sweeps && e_best < o->stall_factor * o->tol) out = ORA_SEG_STALLED;
-    }
+    int out = ora_stop_rule(o, &st, e, i);
     if (out >= 0) { outcome = out; break; }
   }
   if (i > o->max_iters) i = o->max_iters;

@@ -71,7 +71,15 @@ def test_ephemeris_vs_oracle(pc, ora, cfg2):
     pc.eval_ephemeris(plan, _dev(t), rb)
     got = rb.cpu().numpy()
     ref = np.stack([ora.ephem_eval(m, ti) for ti in t], axis=-1)          # [B][3][n]
-    np.testing.assert_array_equal(got, ref)        # same recurrence, each step rounded alike
+    # The oracle sums the series by Clenshaw's recurrence, the library by a
+    # power sum over recurrence-built T_k: the same series in two rounding
+    # orders.  Bound per value: 4 (deg+1) ulps of sum_k |c_k| of its granule,
+    # which a wrong granule, sigma map or axis stride exceeds by many orders.
+    deg = cfg2.coef.shape[3] - 1
+    g = np.clip(np.floor((t - cfg2.t_begin) / cfg2.granule).astype(int), 0, cfg2.coef.shape[1] - 1)
+    scale = np.abs(cfg2.coef[:, g, :, :]).sum(-1).transpose(0, 2, 1)      # [B][3][n]
+    err = np.abs(got - ref)
+    assert (err <= 4 * (deg + 1) * 2.2e-16 * scale).all(), (err / scale).max()
     plan.close()
 
 
@@ -96,14 +104,22 @@ def test_dynamics_vs_oracle(pc, ora, cfg2):
     f = torch.zeros((6, n), dtype=torch.float64, device="cuda")
     pc.eval_dynamics(plan, _dev(t), _dev(y), f)
     got = f.cpu().numpy()
+    deg = cfg2.coef.shape[3] - 1
     for i in range(n):
         ref = ora.dynamics(m, o, t[i], y[:, i])
         np.testing.assert_array_equal(got[:3, i], ref[:3])
-        # rounding bound: a few ulps of each term's magnitude (direct and indirect)
+        # rounding bound: a few ulps of each term's magnitude (direct and
+        # indirect), plus the body-position difference of the two ephemeris
+        # summation orders (bounded as in test_ephemeris_vs_oracle) times the
+        # tidal factor 3 mu_b / |r - r_b|^3 of each body
         rb = ora.ephem_eval(m, t[i])
         r = y[:3, i]
+        g = int(np.clip(np.floor((t[i] - cfg2.t_begin) / cfg2.granule), 0, cfg2.coef.shape[1] - 1))
+        eps_b = 4 * (deg + 1) * 2.2e-16 * np.abs(cfg2.coef[:, g]).sum(-1).max(-1)
         mag = W.MU_SUN / (r @ r) + sum(mu / ((r - p) @ (r - p)) + mu / (p @ p) for mu, p in zip(cfg2.mu, rb))
-        np.testing.assert_allclose(got[3:, i], ref[3:], rtol=0, atol=2e-15 * mag)
+        eph = sum(3 * mu * e / np.linalg.norm(r - p) ** 3 + 3 * mu * e / np.linalg.norm(p) ** 3
+                  for mu, p, e in zip(cfg2.mu, rb, eps_b))
+        np.testing.assert_allclose(got[3:, i], ref[3:], rtol=0, atol=2e-15 * mag + eph)
     plan.close()
 
 
