@@ -201,9 +201,10 @@ pc_status pc_apply_operator(pc_plan *plan, long long n_ic, const double *x0, con
  *   Limit: (4*ceil((N+1)/4) + N + 2) * 6 * 8 * ceil(n_ic/8)*8 bytes must fit in
  *   32 MiB (N = 128: up to 2,664 trajectories); larger n_ic returns PC_EINVAL.
  *   The plan must belong to the current device (else PC_EINVAL).
- *   The first call on a device looks up the array's device address (a one-time
- *   set-up per device, with that device current); make that first call before
- *   any stream capture.
+ *   Every call looks up the array's device address on the current device (a
+ *   lookup, not an allocation); the first call on a device also loads the
+ *   library's device code there, so make that first call before any stream
+ *   capture.
  *   All calls share the one array and it keeps the last call's contents: calls
  *   whose work overlaps on the GPU (different streams, or different host
  *   threads) race on it and must be serialised by the caller. */

@@ -7,8 +7,6 @@
 // caller that must not risk the implicit device synchronisation cudaMalloc and
 // cudaFree can cause.  This entry point stages through a fixed array that is
 // part of the library image instead, and allocates nothing.
-#include <mutex>
-
 #include "pc_internal.h"
 
 namespace {
@@ -18,26 +16,19 @@ namespace {
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch per device.  In host code the array's name
-// is only a host-side stand-in; its device address is looked up once per device
-// with that device current, and that address is what the kernels receive.
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-
+// Device address of g_static_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in; its device address belongs
+// to the current device's context and is looked up, with that device current,
+// on every call (a lookup, not an allocation).  It is not cached: after a
+// cudaDeviceReset or a new primary context the module is loaded again and the
+// address may change.  The first lookup on a device also loads the library's
+// device code there, which is why the first call must come before any stream
+// capture.
 cudaError_t scratch_for_current_device(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
