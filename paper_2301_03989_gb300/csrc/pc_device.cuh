@@ -31,10 +31,8 @@ __device__ __forceinline__ unsigned err_bits32(float e) {
 // granule holding t.  T_0 = 1, T_1 = sigma, T_{k+1} = fma(2 sigma, T_k, -T_{k-1})
 // are formed once per time and shared by every body and axis; each coordinate
 // is then summed from the top degree down with one fused multiply-add per
-// term.  Every step is a single correctly rounded operation, so the body
-// positions are bitwise those of the CPU oracle's evaluation of the same
-// series.  Near a body the force amplifies a position rounding difference by
-// |r| / |r - r_b|, which is why the two must agree exactly.
+// term.  This differs from Clenshaw's recurrence only in rounding: both agree
+// to a few ulps of sum_k |c_k|.
 // ---------------------------------------------------------------------------
 struct EphemLoc {
   int g;

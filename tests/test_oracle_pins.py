@@ -114,8 +114,8 @@ def cfg2():
 
 
 def test_ephem_vs_chebval(ora, cfg2):
-    """Clenshaw evaluation equals numpy's chebval of the same granule (a wrong
-    granule index, sigma map or axis stride fails)."""
+    """The oracle's Clenshaw evaluation equals numpy's chebval of the same
+    granule to rounding (a wrong granule index, sigma map or axis stride fails)."""
     m = ora.Model.from_workload(cfg2)
     rng = np.random.default_rng(0)
     L, tb = cfg2.granule, cfg2.t_begin
