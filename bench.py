@@ -1,14 +1,18 @@
 """Benchmark: trajectories/s of the batched Picard-Chebyshev propagator on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload precision|flyby|uneven|adjoint]
 
-One step = one pc_propagate call over the whole workload: 4096 trajectories
-of the Sun + 8 planets + Moon system, each starting 0.5-1.5 days before a close
-Venus flyby (periapsis 1e4-5e4 km), propagated for 4 years at Chebyshev degree
-128, tol 1e-13 (seeded synthetic stand-in for the paper's 13,509-trajectory
-data set).  Every step runs the whole hot path on the GPU: per-trajectory
-segment schedule, ephemeris at the nodes, Keplerian warm start, force,
-operator contraction, convergence tests, stitching.
+Default workload (the headline pairing): 65,536 trajectories of the Sun +
+Venus + Earth system (a = 0.75 AU, e = 0.3, i = 2 deg, seeded jitter), 2-year
+arcs in 25 segments at Chebyshev degree 128, tol 1e-13.  One step = one
+pc_propagate call over all of them.  The mixed-precision batched path (FP32
+sweeps until the change is below 1e-6, then FP64 sweeps with FP32 correction
+solves, to 1e-13) is the line's value; the plain FP64 GPU sweep runs on the
+same inputs, timed the same way (same steps, graph replay, no per-kernel
+instrumentation), in stats.plain_fp64.  Every step runs the whole hot path on
+the GPU: per-trajectory segment schedule, ephemeris at the nodes, Keplerian
+warm start, force, operator contraction, convergence tests, stitching.
 
 value: trajectories/s with inputs resident in HBM (CUDA events on the launch
 stream, L2 flushed between steps).  e2e: the same through the C ABI with the
@@ -16,15 +20,12 @@ initial states copied from pinned host memory and the final states + status
 copied back inside the timed region.  --impl reference times the CPU oracle
 on a bounded sample of the same workload on the host cores.
 
-The headline path is the mixed-precision batched sweep (FP32 sweeps on the
-deviation from the Keplerian warm start, FP64 sweeps with FP32 correction
-solves between them, to 1e-13); the plain FP64 GPU sweep runs on the same
-inputs and is reported beside it (stats.plain_fp64), with the difference
-between the two results.  --workload precision | uneven | adjoint run the
-65,536-trajectory precision study, the 1,048,576-trajectory uneven batch and
-the reverse-mode workload instead, each printing its own line.
+--workload flyby runs the 4096-trajectory Venus-flyby workload (Sun + 8
+planets + Moon, 4 years, segment halving) with the same pairing; uneven and
+adjoint run the 1,048,576-trajectory uneven batch and the reverse-mode
+workload, each printing its own line.
 
-With N > 1 (torchrun) each rank propagates its own 4096 trajectories (weak
+With N > 1 (torchrun) each rank propagates its own trajectories (weak
 scaling, no data-path collective); rank 0 prints the max-over-ranks time.
 """
 from __future__ import annotations
@@ -45,12 +46,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "trajectories/s (N-body, <=1e-10 rel err): mixed+batched vs plain FP64 GPU"
 UNIT = "trajectories/s"
-IC_PER_RANK = 4096
+IC_PER_RANK = {"precision": 65536, "flyby": 4096}
 
-# DRAM bytes (read + write) of the FP64 contraction per trajectory-sweep, from
-# the ncu capture summarised in profiles/kernels_flyby2048_halfyear_ncu.md
-# (34.6 MB over ~1262 trajectory-sweeps); scaled to a headline launch by its sweeps.
-TRAFFIC_BYTES_PER_SWEEP = 27_422
+# DRAM bytes (read + write) per trajectory-sweep of each kernel, from one ncu
+# capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum over the
+# captured launches / their trajectory-sweeps); None until taken on the current
+# kernel.  A line's traffic is this figure times the launch's sweeps.
+TRAFFIC_BYTES_PER_SWEEP = {"contract": None, "fp32": None}
 
 
 def _peaks():
@@ -171,28 +173,39 @@ def oracle_rate(w, n_sample: int, threads: int):
     return n_sample / dt, dt
 
 
+def headline_workload(args, n_total):
+    """The workload of the paired line: config 3 (precision study) or config 2 (flyby)."""
+    from paper_2301_03989_gb300 import workloads as W
+    if args.workload == "precision":
+        return W.config3(M=n_total)
+    return W.config2(M=n_total, years=args.years)
+
+
+def cpu_sample_note(w, n, secs, cores):
+    arc = "2-year" if w.name.startswith("cfg3") else f"{(w.tf - w.t0) / 31557600.0:g}-year"
+    return f"seeded subset: first {n} of the workload's trajectories, full {arc} arcs, {secs:.1f} s on {cores} threads"
+
+
 def run_reference(args, world, rank):
     """--impl reference: the oracle as it stands on the host cores."""
     if rank != 0:
         return 0
-    from paper_2301_03989_gb300 import workloads as W
     cores = os.cpu_count() or 1
-    w = W.config2(M=IC_PER_RANK)
-    n_sample = args.ref_sample
+    w = headline_workload(args, IC_PER_RANK[args.workload])
+    n_sample = args.ref_sample or (1024 if args.workload == "precision" else 128)
     for _ in range(args.warmup):
-        oracle_rate(w, max(cores, n_sample // 4), cores)
+        oracle_rate(w, max(cores, n_sample // 8), cores)
     times = []
     for _ in range(args.steps):
         _, dt = oracle_rate(w, n_sample, cores)
         times.append(dt)
     ms = 1000.0 * sum(times) / len(times)
     value = n_sample / (ms / 1000.0)
-    sample = f"first {n_sample} of {w.n_ic} trajectories of the workload per step, full 4-year arcs"
+    sample = cpu_sample_note(w, n_sample, ms / 1000.0, cores) + " per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_ic": n_sample, "N": w.N, "arc_years": 4,
-                       "parallelism": "host threads"},
+            "config": {"workload": w.name, "n_ic": n_sample, "N": w.N, "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -204,6 +217,20 @@ def contract_flops_per_sweep(N: int) -> float:
     """Useful FP64 flops of one trajectory-sweep of the contraction: rows 1..N
     of K (row 0 is zero) times N+1 nodes times 6 components, 2 flops each."""
     return 2.0 * N * (N + 1) * 6
+
+
+def fp32_flops_per_sweep(N: int, B: int) -> float:
+    """Useful FP32 flops of one trajectory-sweep of the FP32 phase: the
+    contraction (as above) plus the force, (B+1) pair terms of 20 flops plus a
+    square root and a division per node."""
+    return contract_flops_per_sweep(N) + (N + 1) * (B + 1) * 22.0
+
+
+def fp32_alu_peak_tflops():
+    """FP32 FMA peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x
+    2 flops x the measured maximum SM clock (2070 MHz)."""
+    mhz = _peaks().get("sm_max_mhz", 2070.0)
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, "152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
 
 
 def timed_plain(pc, plan, w, x0, xf, st, it, stream, flush, steps, dev):
@@ -230,8 +257,8 @@ def timed_plain(pc, plan, w, x0, xf, st, it, stream, flush, steps, dev):
 
 def timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, steps, dev):
     """Instrumented replay of the timed steps: a CUDA event on the launch stream
-    between consecutive kernels of every round (direct launches), summed per
-    kernel.  Returns per-step ms, rounds and kernel times."""
+    between consecutive kernels of every round (direct launches, one stream),
+    summed per kernel.  Returns per-step ms, rounds and kernel times."""
     import torch
     pc.set_profiling(plan, True)
     pc.kernel_times(plan)                       # clear
@@ -259,6 +286,33 @@ def rel_errors(a, b):
     return er, ev
 
 
+def kernel_roofline(name, kt, steps, w, B, peaks):
+    """Roofline of one kernel from the instrumented replay: algorithmic flops of
+    the trajectory-sweeps it ran / its summed launch time."""
+    launches, ms = kt[name]
+    if name == "contract":
+        flops = contract_flops_per_sweep(w.N) * kt["sweeps64"]
+        peak, src = peaks["fp64_tensor"]
+        bound, kern, dt = "tensor", "k_contract (FP64 DMMA mma.sync m16n8k4)", "f64"
+        sweeps = kt["sweeps64"]
+    elif name == "fp32":
+        flops = fp32_flops_per_sweep(w.N, B) * kt["sweeps32"]
+        peak, src = peaks["fp32_alu"]
+        bound, kern, dt = "alu", "k_fp32 (FP32 sweeps: force + contraction, both modes)", "f32"
+        sweeps = kt["sweeps32"]
+    else:
+        return None
+    achieved = flops / (ms / 1000.0) / 1e12 if ms > 0 else 0.0
+    tb = TRAFFIC_BYTES_PER_SWEEP.get(name)
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None,
+            "traffic": None if tb is None else tb * sweeps / max(1, launches),
+            "kernel": kern, "dtype": dt, "peak_source": src, "launches": launches,
+            "avg_launch_us": 1000.0 * ms / max(1, launches),
+            "algorithmic_flops_per_launch": flops / max(1, launches),
+            "trajectory_sweeps_per_launch": sweeps / max(1, launches)}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2301_03989_gb300 import build as B
@@ -271,15 +325,17 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     B.build()
-    wall = W.config2(M=args.n_ic * world, years=args.years)
+    wall = headline_workload(args, args.n_ic * world)
     lo, hi = shard(wall.n_ic, world, rank)
     w = wall.subset(np.arange(lo, hi))
     M = w.n_ic
+    nB = len(w.mu)
     mixed = args.precision == "mixed"
+    switch_tol = args.switch_tol if args.switch_tol is not None else (1e-6 if args.workload == "precision" else 0.0)
     torch.cuda.synchronize(dev)
     t_plan = time.perf_counter()
     plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED if mixed else pc.PC_PREC_FP64,
-                                 switch_tol=args.switch_tol)
+                                 switch_tol=switch_tol)
     torch.cuda.synchronize(dev)
     plan_ms = 1000.0 * (time.perf_counter() - t_plan)   # operator build + uploads, reported apart
     stream = torch.cuda.Stream(device=dev)
@@ -307,7 +363,7 @@ def run_ours(args, world, rank, local):
         xf_main = xf.clone()
         status = st.cpu().numpy()
         # per-kernel times: the same steps again with an event between kernels
-        prof_ms, _, ktimes = timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, args.steps, dev)
+        prof_ms, _, ktimes = timed_steps(pc, plan, w, x0, xf, st, it, stream, flush, args.prof_steps, dev)
 
         # end to end through the C ABI with host buffers
         hx0 = torch.as_tensor(W.to_planar(w.x0)).pin_memory()
@@ -328,19 +384,27 @@ def run_ours(args, world, rank, local):
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
 
-        # the plain FP64 GPU sweep on the same inputs (the metric's comparator)
+        # the plain FP64 GPU sweep on the same inputs (the metric's comparator),
+        # timed exactly like the headline: same warm-up and step counts, graph
+        # replay, no instrumentation; then a separate instrumented replay
         plain = None
         if mixed and not args.no_plain:
             plan64 = pc.plan_from_workload(w, precision=pc.PC_PREC_FP64)
             xf64 = torch.zeros_like(x0)
             st64 = torch.zeros_like(st)
             it64 = torch.zeros_like(it)
-            for _ in range(1):
+            if args.autotune:
+                pc.autotune(plan64, x0, w.t0, w.tf, max_rounds=256, stream=stream)
+            for _ in range(args.warmup):
                 pc.propagate(plan64, x0, w.t0, w.tf, xf64, status=st64, iters=it64, stream=stream)
-            ms64, rounds64, kt64 = timed_steps(pc, plan64, w, x0, xf64, st64, it64, stream, flush,
-                                               args.plain_steps, dev)
+            clk64 = ClockSampler(local)
+            clk64.start()
+            ms64, rounds64, _ = timed_plain(pc, plan64, w, x0, xf64, st64, it64, stream, flush, args.steps, dev)
+            clk64 = clk64.stop()
+            _, _, kt64 = timed_steps(pc, plan64, w, x0, xf64, st64, it64, stream, flush, 1, dev)
             er, ev = rel_errors(xf_main.cpu().numpy(), xf64.cpu().numpy())
-            plain = dict(ms=sum(ms64) / len(ms64), kt=kt64, rounds=rounds64 / len(ms64), er=er, ev=ev)
+            plain = dict(ms=sum(ms64) / len(ms64), ms_all=ms64, kt=kt64, rounds=rounds64 / len(ms64), er=er, ev=ev,
+                         clocks=clk64, status=int((st64.cpu().numpy() != 0).sum()))
             plan64.close()
 
     ms = sum(step_ms) / len(step_ms)
@@ -351,53 +415,50 @@ def run_ours(args, world, rank, local):
     value = total_ic / (ms_max / 1000.0)
     e2e_value = total_ic / (e2e_max / 1000.0)
 
-    # roofline of the FP64 tensor-core contraction (the dominant kernel of the FP64 sweeps)
+    # roofline of the dominant kernel (by time in the instrumented replay)
     names = pc.KERNEL_NAMES
-    kname = max(names, key=lambda k: ktimes[k][1])
-    launches_c, ms_c = ktimes["contract"]
-    sweeps64 = ktimes["sweeps64"]
-    flops = contract_flops_per_sweep(w.N) * sweeps64
-    achieved = flops / (ms_c / 1000.0) / 1e12 if ms_c > 0 else 0.0
-    peak, peak_src = fp64_tensor_peak_tflops()
+    peaks = {"fp64_tensor": fp64_tensor_peak_tflops(), "fp32_alu": fp32_alu_peak_tflops()}
     tsum = sum(ktimes[k][1] for k in names)
-    traffic = None if TRAFFIC_BYTES_PER_SWEEP is None else TRAFFIC_BYTES_PER_SWEEP * sweeps64 / max(1, launches_c)
-    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None, "traffic": traffic,
-            "kernel": "k_contract (FP64 DMMA mma.sync m16n8k4)", "dtype": "f64", "peak_source": peak_src,
-            "launches": launches_c, "avg_launch_us": 1000.0 * ms_c / max(1, launches_c),
-            "algorithmic_flops_per_launch": flops / max(1, launches_c),
-            "kernel_share": {k: ktimes[k][1] / max(1e-9, tsum) for k in names},
-            "dominant_by_time": kname,
-            "timing": "CUDA events between consecutive kernels on the launch stream, over an instrumented "
-                      "replay of the timed steps (direct launches)"}
+    kname = max(names, key=lambda k: ktimes[k][1])
+    by_kernel = {k: kernel_roofline(k, ktimes, args.prof_steps, w, nB, peaks) for k in ("contract", "fp32")}
+    roof = by_kernel.get(kname) or by_kernel["contract"]
+    roof = dict(roof, dominant_by_time=kname,
+                kernel_share={k: ktimes[k][1] / max(1e-9, tsum) for k in names},
+                timing="CUDA events between consecutive kernels on the launch stream, over an instrumented replay "
+                       "of the timed steps (direct launches, one stream)")
 
     line = None
     if rank == 0:
         cores = os.cpu_count() or 1
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            rate, secs = oracle_rate(w, min(M, args.cpu_sample), cores)
-            n1 = min(M, max(1, args.cpu_sample // 16))
+            n_cpu = min(M, args.cpu_sample or (4096 if args.workload == "precision" else 256))
+            rate, secs = oracle_rate(w, n_cpu, cores)
+            n1 = min(M, max(1, n_cpu // 16))
             rate1, secs1 = oracle_rate(w, n1, 1)
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"first {min(M, args.cpu_sample)} trajectories of the workload, full "
-                             f"{args.years:g}-year arcs, {secs:.1f} s on {cores} threads",
+                   "sample": cpu_sample_note(w, n_cpu, secs, cores),
                    "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                                      "sample": f"first {n1} trajectories, {secs1:.1f} s"}}
         stats = {"sweep_rounds_per_step": rounds_total / max(1, args.steps),
-                 "trajectory_sweeps_fp64_per_step": sweeps64 / max(1, args.steps),
-                 "trajectory_sweeps_fp32_per_step": ktimes["sweeps32"] / max(1, args.steps),
+                 "trajectory_sweeps_fp64_per_step": ktimes["sweeps64"] / max(1, args.prof_steps),
+                 "trajectory_sweeps_fp32_per_step": ktimes["sweeps32"] / max(1, args.prof_steps),
                  "status_nonzero": int((status != 0).sum()),
-                 "kernel_ms_per_step": {k: ktimes[k][1] / args.steps for k in names},
+                 "kernel_ms_per_step": {k: ktimes[k][1] / args.prof_steps for k in names},
                  "instrumented_ms_per_step": sum(prof_ms) / len(prof_ms),
                  "plan_create_ms": plan_ms,
-                 "ms_per_step_median": statistics.median(step_ms)}
+                 "ms_per_step_all": step_ms,
+                 "ms_per_step_median": statistics.median(step_ms),
+                 "roofline_by_kernel": by_kernel}
         if plain is not None:
             stats["plain_fp64"] = {
                 "value": total_ic / (plain["ms"] / 1000.0), "unit": UNIT, "ms_per_step": plain["ms"],
-                "steps": args.plain_steps, "sweep_rounds_per_step": plain["rounds"],
-                "trajectory_sweeps_fp64_per_step": plain["kt"]["sweeps64"] / max(1, args.plain_steps),
-                "kernel_ms_per_step": {k: plain["kt"][k][1] / args.plain_steps for k in names},
+                "ms_per_step_all": plain["ms_all"], "steps": args.steps, "warmup": args.warmup,
+                "timing": "same as the headline: graph replay, no instrumentation, L2 flushed, CUDA events",
+                "sweep_rounds_per_step": plain["rounds"],
+                "trajectory_sweeps_fp64_per_step": plain["kt"]["sweeps64"],
+                "kernel_ms_per_step_instrumented": {k: plain["kt"][k][1] for k in names},
+                "status_nonzero": plain["status"], "clocks": plain["clocks"],
                 "speedup_mixed_over_plain": plain["ms"] / ms}
             stats["mixed_vs_plain_fp64_rel_err"] = {
                 "pos_max": float(plain["er"].max()), "pos_median": float(np.median(plain["er"])),
@@ -405,11 +466,12 @@ def run_ours(args, world, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_ic_per_gpu": M, "N": w.N, "arc_years": args.years, "tol": w.tol,
+            "vs_baseline": None, "dtype": "mixed fp32->f64" if mixed else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_ic_per_gpu": M, "N": w.N,
+                       "arc_years": round((w.tf - w.t0) / 31557600.0, 3), "tol": w.tol,
                        "path": ("mixed FP32->FP64 batched sweep" if mixed else "plain FP64 batched sweep")
                                + " (per-trajectory segments, compaction, DMMA contraction)",
-                       "switch_tol": args.switch_tol if mixed else None,
+                       "switch_tol": switch_tol if mixed else None,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}",
                        "tuning": tuning},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx0.numel() * 8),
@@ -447,14 +509,13 @@ def _time_calls(fn, steps, warmup, stream, flush, dev):
 
 
 def run_aux(args, world, rank, local):
-    """--workload precision | uneven | adjoint (1 GPU): the precision study
-    (65,536 config-1 trajectories, 2-year arcs, FP32 sweeps to 1e-6 then FP64 to
-    1e-13), uneven batching (up to 1,048,576 trajectories of mixed arc length,
-    degree and segment count, mixed precision, degree groups on concurrent
-    streams) and reverse mode (config-4 flybys: forward pass with tape plus one
+    """--workload uneven | adjoint (1 GPU): uneven batching (up to 1,048,576
+    trajectories of mixed arc length, degree and segment count, degree groups
+    on concurrent streams; mixed precision, or plain FP64 with --precision
+    fp64) and reverse mode (config-4 flybys: forward pass with tape plus one
     reverse sweep).  Each prints one JSON line with its own metric.  Their
     errors against the CPU oracle are checked by the GPU tests
-    (tests/test_gpu_mixed.py, tests/test_gpu_uneven.py), not here."""
+    (tests/test_gpu_uneven.py, tests/test_gpu_adjoint.py), not here."""
     import torch
     from paper_2301_03989_gb300 import build as B
     from paper_2301_03989_gb300 import pcprop as pc
@@ -471,38 +532,7 @@ def run_aux(args, world, rank, local):
     stats, config = {}, {}
     clocks = ClockSampler(local)
     with torch.cuda.stream(stream):
-        if args.workload == "precision":
-            w = W.config3(M=args.n_ic or 65536)
-            M = w.n_ic
-            x0 = torch.as_tensor(W.to_planar(w.x0), device=dev)
-            out = {}
-            for name, prec, sw in (("mixed", pc.PC_PREC_MIXED, 1e-6), ("fp64", pc.PC_PREC_FP64, 0.0)):
-                plan = pc.plan_from_workload(w, precision=prec, switch_tol=sw)
-                xf = torch.zeros_like(x0)
-                st = torch.zeros(M, dtype=torch.int32, device=dev)
-                if name == "mixed":
-                    clocks.start()
-                ms = _time_calls(lambda: pc.propagate(plan, x0, w.t0, w.tf, xf, status=st, stream=stream),
-                                 args.steps, args.warmup, stream, flush, dev)
-                if name == "mixed":
-                    clk = clocks.stop()
-                kt = pc.kernel_times(plan)
-                out[name] = dict(ms=float(np.mean(ms)), xf=W.from_planar(xf.cpu().numpy()),
-                                 status=int((st.cpu().numpy() != 0).sum()), launches=int(kt["kernel_launches"]),
-                                 sweeps64=kt["sweeps64"], sweeps32=kt["sweeps32"])
-                plan.close()
-            ms = out["mixed"]["ms"]
-            n_steps = args.steps + args.warmup
-            stats["plain_fp64"] = {"value": M / (out["fp64"]["ms"] / 1000.0), "ms_per_step": out["fp64"]["ms"],
-                                   "speedup_mixed_over_plain": out["fp64"]["ms"] / ms,
-                                   "trajectory_sweeps_fp64_per_step": out["fp64"]["sweeps64"] / n_steps}
-            stats["mixed_sweeps_per_step"] = {"fp64": out["mixed"]["sweeps64"] / n_steps,
-                                              "fp32": out["mixed"]["sweeps32"] / n_steps}
-            stats["status_nonzero"] = out["mixed"]["status"]
-            launches = out["mixed"]["launches"] // n_steps * args.steps
-            metric = "trajectories/s (config-1 system, 2-year arcs, N=128): mixed FP32->FP64 vs plain FP64 GPU"
-            config = {"workload": w.name, "n_ic": M, "N": w.N, "switch_tol": 1e-6, "tol": w.tol}
-        elif args.workload == "uneven":
+        if args.workload == "uneven":
             uw = W.config5(M=args.n_ic or 1048576)
             M = uw.n_ic
             perm, degs, counts = uw.groups()
@@ -574,7 +604,8 @@ def run_aux(args, world, rank, local):
     line = {"metric": metric, "value": M / (ms_step / 1000.0), "unit": UNIT if args.workload != "adjoint"
             else "trajectory gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": config, "gpu_launches": int(launches),
+            "dtype": "mixed fp32->f64" if args.workload == "uneven" and args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": config, "gpu_launches": int(launches),
             "clocks": clk, "stats": stats}
     print(json.dumps(line))
     return 0
@@ -586,27 +617,33 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=256)
-    ap.add_argument("--ref-sample", type=int, default=128)
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="trajectories in the CPU-baseline sample (default 4096 precision, 256 flyby)")
+    ap.add_argument("--ref-sample", type=int, default=None,
+                    help="trajectories per step of the reference arm (default 1024 precision, 128 flyby)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--switch-tol", type=float, default=0.0,
-                    help="FP32 -> FP64 switch threshold (0: when the FP32 change stops falling)")
+    ap.add_argument("--switch-tol", type=float, default=None,
+                    help="FP32 -> FP64 switch threshold (default 1e-6 precision, 0 flyby: when the FP32 change "
+                         "stops falling)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
-    ap.add_argument("--plain-steps", type=int, default=3)
-    ap.add_argument("--workload", choices=["flyby", "precision", "uneven", "adjoint"], default="flyby",
-                    help="flyby: the headline workload; the others print their own line")
-    ap.add_argument("--n-ic", type=int, default=None, help="trajectories (per GPU for flyby)")
+    ap.add_argument("--prof-steps", type=int, default=2, help="steps of the instrumented per-kernel replay")
+    ap.add_argument("--workload", choices=["precision", "flyby", "uneven", "adjoint"], default="precision",
+                    help="precision: the headline pairing (config 3); flyby: config 2; uneven, adjoint: their own "
+                         "lines")
+    ap.add_argument("--n-ic", type=int, default=None, help="trajectories (per GPU for precision / flyby)")
     ap.add_argument("--years", type=float, default=4.0, help="arc length of the flyby workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":
+        if args.workload not in IC_PER_RANK:
+            args.workload = "precision"
         return run_reference(args, world, rank)
-    if args.workload != "flyby":
+    if args.workload not in IC_PER_RANK:
         return run_aux(args, world, rank, local)
     if args.n_ic is None:
-        args.n_ic = IC_PER_RANK
+        args.n_ic = IC_PER_RANK[args.workload]
     return run_ours(args, world, rank, local)
 
 

@@ -242,7 +242,7 @@ pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
  * Launch shapes of the sweep kernels and the host's round loop.  None of them
  * changes any arithmetic: results are bitwise the same for every setting.
  *   setup_ctas_per_sm     CTAs per SM of the new-segment set-up kernel (1..16)
- *   fp32_ctas_per_sm      CTAs per SM of the FP32 kernels (1..16; one trajectory per CTA at a time)
+ *   fp32_ctas_per_sm      CTAs per SM of the FP32 kernels (1..16)
  *   contract_ctas_per_sm  persistent CTAs per SM of the FP64 contraction (1..16)
  *   rounds_per_batch      sweep rounds queued between two looks at the device's
  *                         done counter (1..64)
@@ -254,8 +254,12 @@ pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
  *                         round (set-up, FP32 phase) on a stream of the device's
  *                         highest priority beside the FP64 branch, 0 at default
  *                         priority
- * Defaults: 4, 4, 4, 8, 8, 1, 1.  Profiling (pc_plan_set_profiling) launches
- * directly whatever `graphs` says. */
+ *   fp32_rows             FP32 kernels: output rows per thread of the tiled
+ *                         kernel (4 or 8), or 0 for one trajectory per CTA
+ *   fp32_slots            FP32 kernels: trajectories per CTA of the tiled kernel
+ *                         (8..64, a multiple of 8; fewer when N is large)
+ * Defaults: 4, 1, 4, 8, 8, 1, 1, 8, 16.  Profiling (pc_plan_set_profiling)
+ * launches directly whatever `graphs` says. */
 typedef struct {
   int setup_ctas_per_sm;
   int fp32_ctas_per_sm;
@@ -264,6 +268,8 @@ typedef struct {
   int repack_div;
   int graphs;
   int side_priority;
+  int fp32_rows;
+  int fp32_slots;
 } pc_tuning;
 
 /* Reads / replaces the plan's tuning (PC_EINVAL on a value out of range). */
@@ -271,8 +277,8 @@ pc_status pc_plan_get_tuning(const pc_plan *plan, pc_tuning *out);
 pc_status pc_plan_set_tuning(pc_plan *plan, const pc_tuning *t);
 
 /* Autotuner: coordinate descent over the tuning fields (contraction CTAs,
- * set-up CTAs, FP32 CTAs, side-branch priority, rounds per batch, compaction
- * threshold, graphs), each
+ * set-up CTAs, FP32 tile shape and CTAs, side-branch priority, rounds per
+ * batch, compaction threshold, graphs), each
  * candidate timed with CUDA events on a propagation of the caller's
  * trajectories x0 (device, planar [6][n_ic]) over [t0, tf] capped at
  * max_rounds sweep rounds (>= 16).  The fastest setting per round is kept in

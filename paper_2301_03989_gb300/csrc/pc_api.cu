@@ -99,6 +99,7 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   s.lc[1] = w.lists + 5 * (size_t)w.ld;
   s.lc_cnt = w.ints + 8;
   s.tile_ctr = w.ints + 7;
+  s.fp32_ctr = w.ints + 10;
   s.cnt64 = w.cnt64;
   s.list_cur = 0;
   s.A = (int)n_ic;
@@ -475,7 +476,9 @@ extern "C" pc_status pc_plan_set_tuning(pc_plan *p, const pc_tuning *t) {
   if (t->setup_ctas_per_sm < 1 || t->setup_ctas_per_sm > 16 || t->fp32_ctas_per_sm < 1 || t->fp32_ctas_per_sm > 16 ||
       t->contract_ctas_per_sm < 1 || t->contract_ctas_per_sm > 16 || t->rounds_per_batch < 1 ||
       t->rounds_per_batch > 64 || t->repack_div < 2 || t->repack_div > 64 || (t->graphs != 0 && t->graphs != 1) ||
-      (t->side_priority != 0 && t->side_priority != 1))
+      (t->side_priority != 0 && t->side_priority != 1) ||
+      (t->fp32_rows != 0 && t->fp32_rows != 4 && t->fp32_rows != 8) || t->fp32_slots < 8 || t->fp32_slots > 64 ||
+      t->fp32_slots % 8 != 0)
     return PC_EINVAL;
   p->tune = *t;
   return PC_OK;
@@ -522,7 +525,13 @@ extern "C" pc_status pc_plan_autotune(pc_plan *p, long long n_ic, const double *
   const std::vector<Axis> axes = {
       {&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8, 12, 16}},
       {&pc_tuning::setup_ctas_per_sm, {2, 4, 8, 16}},
-      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{2, 4, 6, 8, 12} : std::vector<int>{}},
+      // FP32 kernels: one trajectory per CTA wins on short lists (its sweeps
+      // have the shortest latency), the tiled kernel on long ones
+      {&pc_tuning::fp32_rows, mixed ? std::vector<int>{4, 8} : std::vector<int>{}},
+      {&pc_tuning::fp32_slots, mixed ? std::vector<int>{8, 16, 32} : std::vector<int>{}},
+      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{}},
+      {&pc_tuning::fp32_rows, mixed ? std::vector<int>{0} : std::vector<int>{}},
+      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{4, 6, 8, 12} : std::vector<int>{}},
       {&pc_tuning::side_priority, mixed ? std::vector<int>{0, 1} : std::vector<int>{}},
       {&pc_tuning::rounds_per_batch, {4, 8, 16, 32}},
       {&pc_tuning::repack_div, {4, 8, 16}},

@@ -103,6 +103,8 @@ struct Sweep {
   int *lc_cnt;               // [2]
   int list_cur;
   int *tile_ctr;             // dynamic tile counter of the FP64 contraction
+  int *fp32_ctr;             // [2] list-entry counters of the tiled FP32 kernels (new segment, correction),
+                             // cleared by the round's set-up kernel
   unsigned long long *cnt64; // [0] FP64, [1] FP32 trajectory-sweeps of this call
 };
 
@@ -123,7 +125,7 @@ struct Workspace {
   int *lists = nullptr;      // 6 x ld: setup lists [2], FP64 lists [2], correction lists [2]
   int *ints = nullptr;       // [0..1] done counters [finished, stopped], [2..3] setup list counts,
                              // [4] repack count, [5..6] FP64 list counts, [7] tile counter,
-                             // [8..9] correction list counts
+                             // [8..9] correction list counts, [10..11] FP32 list-entry counters
   int *pos = nullptr;        // [ld] repack destinations
   unsigned long long *cnt64 = nullptr;  // [0] FP64 trajectory-sweeps, [1] FP32 trajectory-sweeps
   unsigned long long *h_cnt64 = nullptr;
@@ -157,7 +159,7 @@ struct pc_plan {
   int N = 0, n = 0, kpad = 0, rows_pad = 0;
   int segments = 0;
   pc_options opt{};
-  pc_tuning tune{4, 4, 4, 8, 8, 1, 1};
+  pc_tuning tune{4, 1, 4, 8, 8, 1, 1, 8, 16};
   long long session_id = 0;  // distinguishes calls for the graph cache
   int device = 0;
   // model (device copies)
@@ -168,6 +170,8 @@ struct pc_plan {
   double *d_K = nullptr;
   float *d_K32T = nullptr;   // the operator rounded to FP32 and transposed, [N+1][32 npl]
   int npl = 0;               // ceil((N+1)/32): K32T rows are 32 npl floats long (0: no mixed path)
+  float *d_K32R = nullptr;   // tiled FP32 kernels: [N+1][rows32], K32R[k][r] = K[r+1][k], zero-padded
+  int rows32 = 0;            // 32 ceil(N/32)
   double *d_tau = nullptr;   // [n]
   double *h_K = nullptr;     // host copy, (N+1) x (N+1)
   double *h_tau = nullptr;   // [n]

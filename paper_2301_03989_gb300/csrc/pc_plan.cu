@@ -150,6 +150,15 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
       for (int j = 0; j <= N; j++) Kt[(size_t)k * np + j] = (float)p->h_K[(size_t)j * n + k];
     if (e == cudaSuccess) e = dalloc(&p->d_K32T, Kt.size());
     if (e == cudaSuccess) e = cudaMemcpy(p->d_K32T, Kt.data(), sizeof(float) * Kt.size(), cudaMemcpyHostToDevice);
+    // the same operator for the tiled FP32 kernels: K32R[k][r] = K[r+1][k] for
+    // output rows r = 0..N-1 (nodes 1..N; row 0 of K is zero), rows32 floats
+    // per k, zero-padded
+    p->rows32 = (N + 31) / 32 * 32;
+    std::vector<float> Kr((size_t)n * p->rows32, 0.0f);
+    for (int k = 0; k < n; k++)
+      for (int r = 0; r < N; r++) Kr[(size_t)k * p->rows32 + r] = (float)p->h_K[(size_t)(r + 1) * n + k];
+    if (e == cudaSuccess) e = dalloc(&p->d_K32R, Kr.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_K32R, Kr.data(), sizeof(float) * Kr.size(), cudaMemcpyHostToDevice);
   }
   // Adjoint operator: K transposed without its zero row 0, KTp[j][k'] = K[k'+1][j].
   p->adj_mpad = (n + 15) / 16 * 16;
@@ -316,6 +325,7 @@ extern "C" void pc_plan_destroy(pc_plan *p) {
   cudaFree(p->d_K);
   cudaFree(p->d_KTp);
   cudaFree(p->d_K32T);
+  cudaFree(p->d_K32R);
   cudaFree(p->d_tau);
   cudaFree(p->d_mu);
   cudaFree(p->d_mu32);

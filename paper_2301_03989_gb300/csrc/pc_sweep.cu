@@ -277,6 +277,8 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     s.list_cnt[cur ^ 1] = 0;
     s.l64_cnt[cur ^ 1] = 0;
     s.lc_cnt[cur ^ 1] = 0;
+    s.fp32_ctr[0] = 0;  // this round's FP32 kernels run after this kernel
+    s.fp32_ctr[1] = 0;
   }
   const long long count = s.list_cnt[cur];
   const int *__restrict__ list = s.list[cur];
@@ -861,6 +863,378 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
 }
 
 // ---------------------------------------------------------------------------
+// FP32 sweeps, tiled: the same two modes and the same arithmetic per
+// trajectory as k_fp32, with T trajectories ("slots") per CTA so that one
+// copy of the FP32 operator in shared memory serves all of them.
+//
+// Thread (rg, t) owns output rows rg*R .. rg*R + R - 1 (nodes rg*R + 1 ..
+// rg*R + R; row 0 of K is zero, so node 0 never changes) of slot t: it keeps
+// those nodes' deviations in registers across sweeps, evaluates their force
+// rows (thread rg = 0 also node 0) into the CTA's table G[k][t][6] in shared
+// memory, and accumulates its R x 6 block of K G over k = 0..N in ascending
+// order with one fused multiply-add per term -- the order k_fp32 uses, so
+// every trajectory's result is bitwise that of k_fp32.  A warp is 4 row
+// groups x 8 slots: the operator reads of a warp touch 4 rows (broadcast to 8
+// lanes each), the table reads 8 slots (broadcast to 4 lanes each).
+//
+// Slots are filled from the round's list: slot t of CTA b starts with entry
+// t * gridDim + b (so a short list spreads over all CTAs), and a slot whose
+// trajectory stops takes the next entry from a counter -- converged
+// trajectories leave the working set after every sweep.  The per-slot stop
+// decision is made by thread t after the change and size maxima of the
+// slot's rows are reduced.
+// ---------------------------------------------------------------------------
+constexpr int kFp32tMaxThreads = 256;
+constexpr int kFp32tMaxSlots = 64;
+
+struct Fp32Slots {
+  int e[kFp32tMaxSlots];       // list entry of the slot's trajectory (-1: idle)
+  int m[kFp32tMaxSlots];       // its control slot
+  float w2[kFp32tMaxSlots];    // its omega2
+  int it[kFp32tMaxSlots], nst[kFp32tMaxSlots], stop[kFp32tMaxSlots];
+  float ebest[kFp32tMaxSlots];
+};
+
+// Force row of one node in FP32 (deviation d, node record rc), the arithmetic
+// of k_fp32.
+template <int MODE>
+__device__ __forceinline__ void fp32_force_row(const float4 *__restrict__ rc, int B, const float *__restrict__ mus,
+                                               int indirect, const float d[6], float w2f, float g[6]) {
+  const int boff = MODE == FP32_KEPLER ? 3 : 4;
+  const float4 rk = rc[0];
+  const float d0 = d[0], d1 = d[1], d2 = d[2];
+  const float rr = rk.x * rk.x + rk.y * rk.y + rk.z * rk.z;
+  const float F = encke_F((d0 * (2.0f * rk.x + d0) + d1 * (2.0f * rk.y + d1) + d2 * (2.0f * rk.z + d2)) / rr);
+  float a0 = rk.w * (F * (rk.x + d0) - d0);
+  float a1 = rk.w * (F * (rk.y + d1) - d1);
+  float a2 = rk.w * (F * (rk.z + d2) - d2);
+  for (int b = 0; b < B; b++) {
+    const float4 D = rc[boff + b];
+    if (MODE == FP32_KEPLER) {
+      const float x0 = D.x + d0, x1 = D.y + d1, x2 = D.z + d2;
+      const float ds = rsqrtf(x0 * x0 + x1 * x1 + x2 * x2);
+      const float kb = mus[b] * ds * ds * ds;
+      a0 -= kb * x0;
+      a1 -= kb * x1;
+      a2 -= kb * x2;
+    } else {
+      const float dd = D.x * D.x + D.y * D.y + D.z * D.z;
+      const float Fb = encke_F((d0 * (2.0f * D.x + d0) + d1 * (2.0f * D.y + d1) + d2 * (2.0f * D.z + d2)) / dd);
+      a0 += D.w * (Fb * (D.x + d0) - d0);
+      a1 += D.w * (Fb * (D.y + d1) - d1);
+      a2 += D.w * (Fb * (D.z + d2) - d2);
+    }
+  }
+  if (MODE == FP32_KEPLER && indirect) {
+    const float4 ai = rc[2];
+    a0 -= ai.x;
+    a1 -= ai.y;
+    a2 -= ai.z;
+  }
+  g[0] = w2f * d[3];
+  g[1] = w2f * d[4];
+  g[2] = w2f * d[5];
+  g[3] = w2f * a0;
+  g[4] = w2f * a1;
+  g[5] = w2f * a2;
+}
+
+// Correction-solve node record (k_fp32's CORR layout, with the node's
+// residual) of node j of trajectory m, written to rec.
+__device__ __forceinline__ void fp32_corr_record(const Sweep &s, const Model &md, const float *__restrict__ mus,
+                                                 const double *__restrict__ Yc, const double *__restrict__ E,
+                                                 const float *__restrict__ R32, int j, int m, float4 *rec) {
+  const int ld = s.ld, B = md.B;
+  const size_t yb = (size_t)j * 6 * ld + m;
+  double base[6];
+  float res[6];
+#pragma unroll
+  for (int q = 0; q < 6; q++) {
+    res[q] = (j == 0) ? 0.0f : R32[yb + (size_t)q * ld];
+    base[q] = Yc[yb + (size_t)q * ld] - (double)res[q];
+  }
+  const float bx = (float)base[0], by = (float)base[1], bz = (float)base[2];
+  const float ir = rsqrtf(bx * bx + by * by + bz * bz);
+  rec[0] = make_float4(bx, by, bz, (float)md.mu_c * ir * ir * ir);
+  rec[1] = make_float4((float)base[3], (float)base[4], (float)base[5], 0.0f);
+  rec[2] = make_float4(res[0], res[1], res[2], res[3]);
+  rec[3] = make_float4(res[4], res[5], 0.0f, 0.0f);
+  for (int b = 0; b < B; b++) {
+    const double *eb = E + (size_t)(j * B + b) * 3 * ld + m;
+    const float dx = (float)(base[0] - eb[0]), dy = (float)(base[1] - eb[(size_t)ld]),
+                dz = (float)(base[2] - eb[(size_t)2 * ld]);
+    const float id = rsqrtf(dx * dx + dy * dy + dz * dz);
+    rec[4 + b] = make_float4(dx, dy, dz, mus[b] * id * id * id);
+  }
+}
+
+// Shared-memory bytes of the tiled FP32 kernel: operator (when staged), force
+// table, reduction partials, GMs.
+__host__ __device__ inline size_t fp32t_smem_bytes(int n, int rows32, int T, int RG, bool ksm, int B) {
+  return sizeof(float) * ((ksm ? (size_t)n * rows32 : 0) + (size_t)n * 6 * T + 2 * (size_t)T * (RG / 4) + B + 4);
+}
+
+template <int MODE, int R, bool KSM>
+__global__ void __launch_bounds__(kFp32tMaxThreads, 1)
+    k_fp32t(Sweep s, Ctl c, Model md, const float *__restrict__ K32R, int rows32, const float *__restrict__ mu32,
+            const double *__restrict__ Yc, double *__restrict__ Yn, const double *__restrict__ E,
+            const float *__restrict__ R32, Mix mx, int T) {
+  extern __shared__ float4 fp32t_sm4[];
+  __shared__ Fp32Slots sl;
+  const int N = s.N, n = s.n, ld = s.ld, B = md.B;
+  const int RG = blockDim.x / T, RG4 = RG / 4;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int rg_hi = wid % RG4, rg = rg_hi * 4 + (lane & 3), t = (wid / RG4) * 8 + (lane >> 2);
+  float *Ks = reinterpret_cast<float *>(fp32t_sm4);          // [n][rows32] when KSM
+  float *Gs = Ks + (KSM ? (size_t)n * rows32 : 0);             // [n][T][6]
+  float *red = Gs + (size_t)n * 6 * T;                         // [2][T][RG4]
+  float *mus = red + 2 * T * RG4;                              // [B]
+  const int cur = s.list_cur;
+  const int count = MODE == FP32_KEPLER ? s.list_cnt[cur] : s.lc_cnt[cur];
+  const int *list = MODE == FP32_KEPLER ? s.list[cur] : s.lc[cur];
+  if ((int)blockIdx.x >= count) return;  // no entry for this CTA, now or later
+  int *ctr = s.fp32_ctr + (MODE == FP32_KEPLER ? 0 : 1);
+  const int first_refill = gridDim.x * T;
+
+  if (KSM)
+    for (int i = tid; i < n * rows32 / 4; i += blockDim.x)
+      reinterpret_cast<float4 *>(Ks)[i] = __ldg(reinterpret_cast<const float4 *>(K32R) + i);
+  for (int b = tid; b < B; b += blockDim.x) mus[b] = mu32[b];
+  if (tid < T) {
+    const int e = tid * gridDim.x + blockIdx.x;
+    const bool ok = e < count;
+    sl.e[tid] = ok ? e : -1;
+    sl.m[tid] = ok ? list[e] : 0;
+    sl.w2[tid] = ok ? (float)c.w2[list[e]] : 0.0f;
+    sl.it[tid] = 0;
+    sl.nst[tid] = 0;
+    sl.stop[tid] = 0;
+    sl.ebest[tid] = __int_as_float(0x7f800000);
+  }
+  __syncthreads();
+
+  const int j0 = rg * R + 1;  // first node of the thread's rows
+  const float *Kk = KSM ? Ks + rg * R : K32R + rg * R;
+  const float *Gk = Gs + t * 6;
+  int e = sl.e[t];
+  int m = sl.m[t];
+  float w2f = sl.w2[t];
+  bool fresh = true;
+  float dl[R][6], acc[R][6];
+  for (;;) {
+    const bool live = e >= 0;
+    if (live && fresh) {
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int q = 0; q < 6; q++) dl[i][q] = 0.0f;
+      if (MODE == FP32_CORR) {
+        // node records from the FP64 iterate, its residual and the body positions
+        float4 *rb = reinterpret_cast<float4 *>(mx.X32 + (size_t)e * n * mx.xs);
+        if (rg == 0) fp32_corr_record(s, md, mus, Yc, E, R32, 0, m, rb);
+        for (int i = 0; i < R; i++)
+          if (j0 + i <= N) fp32_corr_record(s, md, mus, Yc, E, R32, j0 + i, m, rb + (size_t)(j0 + i) * (mx.xs / 4));
+      }
+    }
+    fresh = false;
+    // force rows of the thread's nodes
+    if (live) {
+      const float4 *rb = reinterpret_cast<const float4 *>(mx.X32 + (size_t)e * n * mx.xs);
+      float g[6];
+      if (rg == 0) {
+        const float z[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        fp32_force_row<MODE>(rb, B, mus, md.indirect, z, w2f, g);
+        float2 *gp = reinterpret_cast<float2 *>(Gs + t * 6);
+        gp[0] = make_float2(g[0], g[1]);
+        gp[1] = make_float2(g[2], g[3]);
+        gp[2] = make_float2(g[4], g[5]);
+      }
+#pragma unroll
+      for (int i = 0; i < R; i++) {
+        const int j = j0 + i;
+        if (j <= N) {
+          fp32_force_row<MODE>(rb + (size_t)j * (mx.xs / 4), B, mus, md.indirect, dl[i], w2f, g);
+          float2 *gp = reinterpret_cast<float2 *>(Gs + ((size_t)j * T + t) * 6);
+          gp[0] = make_float2(g[0], g[1]);
+          gp[1] = make_float2(g[2], g[3]);
+          gp[2] = make_float2(g[4], g[5]);
+        }
+      }
+    }
+    __syncthreads();
+    // the thread's R x 6 block of K G, k ascending
+    float emax = 0.0f, dmax = 0.0f;
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int q = 0; q < 6; q++) acc[i][q] = 0.0f;
+#pragma unroll 2
+      for (int k = 0; k < n; k++) {
+        float kv[R];
+#pragma unroll
+        for (int i = 0; i < R; i += 4) {
+          const float4 k4 = KSM ? *reinterpret_cast<const float4 *>(Kk + (size_t)k * rows32 + i)
+                                : __ldg(reinterpret_cast<const float4 *>(Kk + (size_t)k * rows32 + i));
+          kv[i] = k4.x;
+          kv[i + 1] = k4.y;
+          kv[i + 2] = k4.z;
+          kv[i + 3] = k4.w;
+        }
+        const float2 *g2 = reinterpret_cast<const float2 *>(Gk + (size_t)k * 6 * T);
+        const float2 ga = g2[0], gb = g2[1], gc = g2[2];
+#pragma unroll
+        for (int i = 0; i < R; i++) {
+          acc[i][0] = fmaf(kv[i], ga.x, acc[i][0]);
+          acc[i][1] = fmaf(kv[i], ga.y, acc[i][1]);
+          acc[i][2] = fmaf(kv[i], gb.x, acc[i][2]);
+          acc[i][3] = fmaf(kv[i], gb.y, acc[i][3]);
+          acc[i][4] = fmaf(kv[i], gc.x, acc[i][4]);
+          acc[i][5] = fmaf(kv[i], gc.y, acc[i][5]);
+        }
+      }
+      // change and size of the deviation, relative to the iterate
+      const float4 *rb = reinterpret_cast<const float4 *>(mx.X32 + (size_t)e * n * mx.xs);
+#pragma unroll
+      for (int i = 0; i < R; i++) {
+        const int j = j0 + i;
+        if (j <= N) {
+          const float4 *rj = rb + (size_t)j * (mx.xs / 4);
+          const float4 rk = rj[0], vk = rj[1];
+          const float yk[6] = {rk.x, rk.y, rk.z, vk.x, vk.y, vk.z};
+          float res[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          if (MODE == FP32_CORR) {
+            const float4 ra = rj[2], rv = rj[3];
+            res[0] = ra.x; res[1] = ra.y; res[2] = ra.z; res[3] = ra.w; res[4] = rv.x; res[5] = rv.y;
+          }
+          float d[6], y[6], cn[6];
+#pragma unroll
+          for (int q = 0; q < 6; q++) {
+            cn[q] = res[q] + acc[i][q];
+            d[q] = cn[q] - dl[i][q];
+            y[q] = yk[q] + cn[q];
+            dl[i][q] = cn[q];
+          }
+          float dr = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          float dv = sqrtf(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+          float mr = sqrtf(cn[0] * cn[0] + cn[1] * cn[1] + cn[2] * cn[2]);
+          float mv = sqrtf(cn[3] * cn[3] + cn[4] * cn[4] + cn[5] * cn[5]);
+          if (s.relative) {
+            const float nr = sqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+            const float nv = sqrtf(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
+            if (nr > 0.0f) { dr /= nr; mr /= nr; }
+            if (nv > 0.0f) { dv /= nv; mv /= nv; }
+          }
+          emax = nanmaxf(emax, nanmaxf(dr, dv));
+          dmax = fmaxf(dmax, fmaxf(mr, mv));
+        }
+      }
+    }
+    // maxima over the slot's row groups: 4 lanes of the warp, then RG4 warps
+    emax = nanmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+    dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, 1));
+    emax = nanmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+    dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, 2));
+    if ((lane & 3) == 0) {
+      red[t * RG4 + rg_hi] = emax;
+      red[(T + t) * RG4 + rg_hi] = dmax;
+    }
+    __syncthreads();
+    // stop decision per slot (k_fp32's rules), bookkeeping, next entry
+    bool more = false;
+    if (tid < T && sl.e[tid] >= 0) {
+      float em = 0.0f, dm = 0.0f;
+      for (int h = 0; h < RG4; h++) {
+        em = nanmaxf(em, red[tid * RG4 + h]);
+        dm = fmaxf(dm, red[(T + tid) * RG4 + h]);
+      }
+      const int it = sl.it[tid] + 1;
+      sl.it[tid] = it;
+      int stop = 0;
+      if (!((double)em <= s.div_limit)) {
+        stop = 2;
+      } else {
+        int nst = sl.nst[tid];
+        const float eb = sl.ebest[tid];
+        nst = (em < 0.5f * eb) ? 0 : nst + 1;
+        sl.nst[tid] = nst;
+        sl.ebest[tid] = fminf(eb, em);
+        if ((MODE == FP32_KEPLER && (double)em < s.switch_tol) || em < kFp32Floor * dm || nst >= 2 ||
+            it >= s.max_iters)
+          stop = 1;
+      }
+      sl.stop[tid] = stop;
+      if (stop) {
+        const int mm = sl.m[tid];
+        c.sweeps[mm] += it;
+        atomicAdd(s.cnt64 + 1, (unsigned long long)it);
+        if (MODE == FP32_KEPLER) {
+          if (stop == 2) {
+            c.err32[mm] = err_bits32(em);
+          } else {
+            c.phase[mm] = PH_READY64;
+            c.seg_sweeps[mm] = 0;
+            c.nstall[mm] = 0;
+            c.e_best[mm] = __longlong_as_double(0x7FF0000000000000LL);
+          }
+        } else {
+          if (stop == 2) c.ncorr[mm] = s.max_corr;
+          c.phase[mm] = PH_READY64;
+        }
+        const int nx = first_refill + atomicAdd(ctr, 1);
+        const bool ok = nx < count;
+        sl.e[tid] = ok ? nx : -1;
+        sl.m[tid] = ok ? list[nx] : 0;
+        sl.w2[tid] = ok ? (float)c.w2[list[nx]] : 0.0f;
+        sl.it[tid] = 0;
+        sl.nst[tid] = 0;
+        sl.ebest[tid] = __int_as_float(0x7f800000);
+      }
+      more = sl.e[tid] >= 0;
+    }
+    const bool any = __syncthreads_or(more);
+    // a stopped slot writes its trajectory's result and takes the next one
+    if (live && sl.stop[t]) {
+      const bool fail = sl.stop[t] == 2;
+      if (MODE == FP32_KEPLER) {
+        if (!fail) {
+          const double *yk = mx.YK + (size_t)e * n * 6;
+          if (rg == 0)
+#pragma unroll
+            for (int q = 0; q < 6; q++) Yn[(size_t)q * ld + m] = yk[q] + (double)0.0f;
+#pragma unroll
+          for (int i = 0; i < R; i++) {
+            const int j = j0 + i;
+            if (j <= N)
+#pragma unroll
+              for (int q = 0; q < 6; q++) Yn[((size_t)j * 6 + q) * ld + m] = yk[(size_t)j * 6 + q] + (double)dl[i][q];
+          }
+        }
+      } else {
+        if (rg == 0)
+#pragma unroll
+          for (int q = 0; q < 6; q++) Yn[(size_t)q * ld + m] = Yc[(size_t)q * ld + m] + (double)0.0f;
+#pragma unroll
+        for (int i = 0; i < R; i++) {
+          const int j = j0 + i;
+          if (j <= N)
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+              const size_t o = ((size_t)j * 6 + q) * ld + m;
+              Yn[o] = Yc[o] + (fail ? 0.0 : (double)acc[i][q]);
+            }
+        }
+      }
+      e = sl.e[t];
+      m = sl.m[t];
+      w2f = sl.w2[t];
+      fresh = true;
+    }
+    if (!any) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Resolution test (Chebyshev tail of the force fit).  On the CGL nodes
 // T_N(tau_j) = (-1)^(N+j) and T_{N-1}(tau_j) = (-1)^(N+j) tau_j, so the two
 // top coefficients of the interpolant of g are
@@ -1157,15 +1531,71 @@ size_t fp32_smem_bytes(const pc_plan *p) {
   return sizeof(float) * ((size_t)p->n * (xss + 6) + 2 * (threads / 32));
 }
 
-// FP32 sweeps of one mode over this round's list: CTAs of 32 ceil((N+1)/32) threads.
+// Launch shape of the tiled FP32 kernel under the plan's tuning: R rows per
+// thread, RG = 4 ceil(N / 4R) row groups, T slots (a multiple of 8, at most
+// 256 / RG threads' worth), the operator staged in shared memory when it fits.
+// ok = 0 when even 8 slots exceed 256 threads (N > 256): one trajectory per
+// CTA then.
+struct Fp32tShape {
+  int R, RG, T, threads;
+  bool ksm, ok;
+  size_t smem;
+};
+constexpr size_t kMaxDynSmem = 220 * 1024;
+
+Fp32tShape fp32t_shape(const pc_plan *p) {
+  Fp32tShape sh{};
+  const int N = p->N;
+  sh.R = p->tune.fp32_rows == 4 ? 4 : 8;
+  sh.RG = 4 * ((N + 4 * sh.R - 1) / (4 * sh.R));
+  if (sh.R == 4 && sh.RG * 8 > kFp32tMaxThreads) {
+    sh.R = 8;
+    sh.RG = 4 * ((N + 31) / 32);
+  }
+  sh.ok = p->tune.fp32_rows != 0 && sh.RG * 8 <= kFp32tMaxThreads;
+  const int tmax = std::min(kFp32tMaxSlots, std::max(8, kFp32tMaxThreads / sh.RG / 8 * 8));
+  sh.T = std::max(8, std::min(p->tune.fp32_slots / 8 * 8, tmax));
+  sh.threads = sh.RG * sh.T;
+  sh.ksm = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, true, p->model.B) <= kMaxDynSmem;
+  sh.smem = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, sh.ksm, p->model.B);
+  return sh;
+}
+
+template <int MODE, int R, bool KSM>
+void launch_fp32t_one(const pc_plan *p, const Fp32tShape &sh, const Sweep &s, const double *Yc, double *Yn,
+                      const double *E, const float *R32, const Mix &mx, cudaStream_t st) {
+  const Ctl &c = p->ws.ctl[p->ws.live];
+  k_fp32t<MODE, R, KSM><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), sh.threads, sh.smem, st>>>(
+      s, c, p->model, p->d_K32R, p->rows32, p->d_mu32, Yc, Yn, E, R32, mx, sh.T);
+}
+
+template <int MODE, int R, bool KSM>
+cudaError_t fp32t_attr(size_t smem) {
+  return cudaFuncSetAttribute(k_fp32t<MODE, R, KSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// FP32 sweeps of one mode over this round's list: the tiled kernel (T
+// trajectories per CTA), or with fp32_rows = 0 one trajectory per CTA of
+// 32 ceil((N+1)/32) threads.  Both give bitwise the same results.
 template <int MODE>
 void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn, const double *E, const float *R32,
                  const Mix &mx, cudaStream_t st) {
-  const int threads = 32 * ((p->n + 31) / 32);
-  const size_t smem = fp32_smem_bytes(p);
-  const Ctl &c = p->ws.ctl[p->ws.live];
-  k_fp32<MODE><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), threads, smem, st>>>(s, c, p->model, p->d_K32T, p->d_mu32, Yc,
-                                                                           Yn, E, R32, mx);
+  const Fp32tShape sh = fp32t_shape(p);
+  if (!sh.ok) {
+    const int threads = 32 * ((p->n + 31) / 32);
+    const size_t smem = fp32_smem_bytes(p);
+    const Ctl &c = p->ws.ctl[p->ws.live];
+    k_fp32<MODE><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), threads, smem, st>>>(s, c, p->model, p->d_K32T, p->d_mu32,
+                                                                             Yc, Yn, E, R32, mx);
+    return;
+  }
+  if (sh.R == 4) {
+    if (sh.ksm) launch_fp32t_one<MODE, 4, true>(p, sh, s, Yc, Yn, E, R32, mx, st);
+    else launch_fp32t_one<MODE, 4, false>(p, sh, s, Yc, Yn, E, R32, mx, st);
+  } else {
+    if (sh.ksm) launch_fp32t_one<MODE, 8, true>(p, sh, s, Yc, Yn, E, R32, mx, st);
+    else launch_fp32t_one<MODE, 8, false>(p, sh, s, Yc, Yn, E, R32, mx, st);
+  }
 }
 
 }  // namespace
@@ -1176,6 +1606,21 @@ cudaError_t prepare_launches(const pc_plan *p) {
   const int bytes = (int)fp32_smem_bytes(p);
   cudaError_t e = cudaFuncSetAttribute(k_fp32<FP32_KEPLER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fp32<FP32_CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const Fp32tShape sh = fp32t_shape(p);
+  if (e != cudaSuccess || !sh.ok) return e;
+  if (sh.R == 4 && sh.ksm) {
+    e = fp32t_attr<FP32_KEPLER, 4, true>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 4, true>(sh.smem);
+  } else if (sh.R == 4) {
+    e = fp32t_attr<FP32_KEPLER, 4, false>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 4, false>(sh.smem);
+  } else if (sh.ksm) {
+    e = fp32t_attr<FP32_KEPLER, 8, true>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 8, true>(sh.smem);
+  } else {
+    e = fp32t_attr<FP32_KEPLER, 8, false>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 8, false>(sh.smem);
+  }
   return e;
 }
 
@@ -1299,7 +1744,7 @@ cudaError_t launch_apply_operator(const pc_plan *p, long long n_ic, int ld, cons
   Ctl c = w.ctl[w.live];
   c.x = const_cast<double *>(x0);
   const long long tiles = (long long)(s.rows_pad / 16) * ((n_ic + 7) / 8);
-  k_contract_diag<<<(unsigned)std::min<long long>(tiles, 152 * 8), 32 * kSplit, 0, st>>>(s, c, p->d_K, G, Y);
+  k_contract_diag<<<(unsigned)std::min<long long>(tiles, sm_ctas(p, 8)), 32 * kSplit, 0, st>>>(s, c, p->d_K, G, Y);
   return cudaGetLastError();
 }
 

@@ -43,10 +43,11 @@ def test_mixed_config3_subset_vs_oracle(pc, ora):
 def test_precision_study_error_report(pc, ora):
     """Config 3 at full size (65,536 trajectories, 2-year arcs, N = 128), FP32
     sweeps until the change is below 1e-6 then FP64 to 1e-13, and the plain FP64
-    path: per-trajectory error against the oracle on a seeded sample of 512."""
+    path: per-trajectory error against the oracle on a seeded subset of 4096
+    trajectories."""
     import os
     w = W.config3()
-    idx = np.sort(np.random.default_rng(0).choice(w.n_ic, size=512, replace=False))
+    idx = np.sort(np.random.default_rng(0).choice(w.n_ic, size=4096, replace=False))
     o = run_oracle(ora, w, w.x0[idx], threads=os.cpu_count() or 8)
     for name, prec, sw in (("mixed", pc.PC_PREC_MIXED, 1e-6), ("fp64", pc.PC_PREC_FP64, 0.0)):
         g = run_gpu(pc, w, w.x0, precision=prec, switch_tol=sw)

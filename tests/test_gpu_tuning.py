@@ -8,6 +8,9 @@ from paper_2301_03989_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+DEFAULT_TUNING = dict(setup_ctas_per_sm=4, fp32_ctas_per_sm=1, contract_ctas_per_sm=4, rounds_per_batch=8,
+                      repack_div=8, graphs=1, side_priority=1, fp32_rows=8, fp32_slots=16)
+
 
 @pytest.fixture(scope="module")
 def pc():
@@ -43,14 +46,16 @@ def test_tunings_and_graphs_are_bitwise_neutral(pc, precision):
     settings = [dict(graphs=0), dict(graphs=1, rounds_per_batch=2), dict(contract_ctas_per_sm=1, setup_ctas_per_sm=1),
                 dict(contract_ctas_per_sm=8, fp32_ctas_per_sm=16, setup_ctas_per_sm=16),
                 dict(repack_div=2, rounds_per_batch=16), dict(repack_div=64, rounds_per_batch=5, graphs=1),
-                dict(side_priority=0, contract_ctas_per_sm=16)]
+                dict(side_priority=0, contract_ctas_per_sm=16),
+                # FP32 kernels: one trajectory per CTA, and tiles of 4 / 8 rows per thread with 8..64 slots
+                dict(fp32_rows=0, fp32_ctas_per_sm=4), dict(fp32_rows=4, fp32_slots=8, fp32_ctas_per_sm=2),
+                dict(fp32_rows=8, fp32_slots=32), dict(fp32_rows=4, fp32_slots=64, fp32_ctas_per_sm=3)]
     for kw in settings:
         pc.set_tuning(plan, **kw)
         r = _run(pc, plan, w, x0d, tf)
         for a, b in zip(base[2:], r[2:]):
             assert torch.equal(a, b), kw
-        pc.set_tuning(plan, setup_ctas_per_sm=4, fp32_ctas_per_sm=4, contract_ctas_per_sm=4, rounds_per_batch=8,
-                      repack_div=8, graphs=1, side_priority=1)
+        pc.set_tuning(plan, **DEFAULT_TUNING)
     # the caller's own (non-default) stream: no fork, graph captured on it directly
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
@@ -64,11 +69,11 @@ def test_tuning_validation(pc):
     w = W.config1(M=8)
     plan = pc.plan_from_workload(w)
     for bad in (dict(setup_ctas_per_sm=0), dict(contract_ctas_per_sm=17), dict(rounds_per_batch=0),
-                dict(repack_div=1), dict(graphs=2), dict(fp32_ctas_per_sm=17), dict(side_priority=2)):
+                dict(repack_div=1), dict(graphs=2), dict(fp32_ctas_per_sm=17), dict(side_priority=2),
+                dict(fp32_rows=2), dict(fp32_slots=12), dict(fp32_slots=0), dict(fp32_slots=72)):
         with pytest.raises(pc.PCError):
             pc.set_tuning(plan, **bad)
-    assert pc.get_tuning(plan) == dict(setup_ctas_per_sm=4, fp32_ctas_per_sm=4, contract_ctas_per_sm=4,
-                                       rounds_per_batch=8, repack_div=8, graphs=1, side_priority=1)
+    assert pc.get_tuning(plan) == DEFAULT_TUNING
     plan.close()
 
 
