@@ -118,12 +118,21 @@ def test_config2_short_arc_end_to_end(pc, ora):
     assert (g["nseg"] > 3).all()        # the flyby forced halving
 
 
-def _segment_local(ora, w, g, idx):
+def pmap(fn, items):
+    """Runs fn over items on the host's cores (the oracle's C calls release the GIL)."""
+    import concurrent.futures as cf
+    import os
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
+        return list(ex.map(fn, items))
+
+
+def _segment_local(ora, w, g, idx, tf=None):
     """Oracle restarted at the GPU's checkpoints; returns max relative error at
     the next checkpoint (or the end state)."""
     m = ora.Model.from_workload(w)
     o = ora.Opts(N=w.N, segments=1, seg_mode=0, tol=w.tol, max_iters=w.max_iters, max_depth=0, trunc_tol=0.0)
-    worst = 0.0
+    tf = w.tf if tf is None else tf
+    jobs = []
     for i in idx:
         ns = int(g["nseg"][i])
         ck = g["ckpt"][i]
@@ -132,16 +141,37 @@ def _segment_local(ora, w, g, idx):
             if s + 1 < ns:
                 tb, xb = ck[s + 1, 0], ck[s + 1, 1:]
             else:
-                tb, xb = w.tf, g["xf"][i]
-            r = ora.propagate(m, o, xa[None], ta, tb)
-            er, ev = rel_err(r["xf"], xb[None])
-            worst = max(worst, er[0], ev[0])
-    return worst
+                tb, xb = tf, g["xf"][i]
+            jobs.append((ta, xa, tb, xb))
+
+    def one(job):
+        ta, xa, tb, xb = job
+        r = ora.propagate(m, o, xa[None], ta, tb)
+        er, ev = rel_err(r["xf"], xb[None])
+        return max(er[0], ev[0])
+    return max(pmap(one, jobs), default=0.0)
+
+
+def stm_rel_norm(ora, w, x0, bounds):
+    """2-norm of the oracle's state-transition matrix over the given segment
+    bounds, in relative units (rows scaled by 1/|r_f| or 1/|v_f|, columns by
+    |r_0| or |v_0|): the factor by which a relative error at the start grows
+    by the end."""
+    m = ora.Model.from_workload(w)
+    o = ora.Opts(N=w.N, tol=w.tol, max_iters=w.max_iters)
+    xf, Phi, capped, _ = ora.stm_propagate(m, o, x0, bounds)
+    s0 = np.r_[[np.linalg.norm(x0[:3])] * 3, [np.linalg.norm(x0[3:])] * 3]
+    sf = np.r_[[np.linalg.norm(xf[:3])] * 3, [np.linalg.norm(xf[3:])] * 3]
+    return float(np.linalg.norm(Phi * s0[None, :] / sf[:, None], 2)), capped
 
 
 def test_config2_full_arc_segment_local(pc, ora):
     """16 ICs over the full 4-year arc: statuses agree; each GPU segment matches
-    the oracle's segment started from the same checkpoint."""
+    the oracle's segment started from the same checkpoint.  End to end, every
+    trajectory whose GPU-oracle gap exceeds 1e-10 is printed with the oracle's
+    state-transition norm over its arc (in relative units), and the gap must
+    stay below 1e-13 times that norm: a tolerance-level difference at the start
+    of the arc, grown by the flybys."""
     w = W.config2(M=16)
     g = run_gpu(pc, w, w.x0, max_ckpt=600)
     assert g["code"] == pc.PC_OK
@@ -150,19 +180,34 @@ def test_config2_full_arc_segment_local(pc, ora):
     o = run_oracle(ora, w, w.x0)
     np.testing.assert_array_equal(g["status"], o["status"])
     er, ev = rel_err(g["xf"], o["xf"])
-    # end to end the flyby amplifies round-off; report-only bound
-    assert er.max() < 1e-6 and ev.max() < 1e-6
+    gap = np.maximum(er, ev)
+    big = np.flatnonzero(gap > TOL)
+
+    def norm(i):
+        k = int(g["nseg"][i])
+        bounds = np.r_[g["ckpt"][i, :k, 0], w.tf]
+        return stm_rel_norm(ora, w, w.x0[i], bounds)
+    norms = pmap(norm, big)
+    for i, (nrm, capped) in zip(big, norms):
+        print(f"config 2 trajectory {i}: end-to-end gap {gap[i]:.2e}, oracle STM norm (relative) {nrm:.2e}, "
+              f"gap / norm {gap[i] / nrm:.2e}, segments {int(g['nseg'][i])}")
+        assert capped == 0
+        assert gap[i] < 1e-13 * nrm, (i, gap[i], nrm)
+    print(f"config 2 end to end: {big.size} of {w.n_ic} above 1e-10; median gap {np.median(gap):.2e}")
 
 
 def test_config2_full_size_sampled(pc, ora):
-    """The full 4096-IC, 4-year workload in the benchmark's launch
-    configuration; sampled trajectories checked segment by segment."""
+    """The full 4096-IC, 4-year workload in the launch configuration the
+    benchmark uses for it; 64 seeded trajectories checked segment by segment."""
     w = W.config2()
     g = run_gpu(pc, w, w.x0, max_ckpt=600)
     assert g["code"] == pc.PC_OK
     assert (g["status"] & (pc.PC_IC_NOT_CONVERGED | pc.PC_IC_NONFINITE) == 0).all()
-    idx = np.random.default_rng(11).choice(w.n_ic, 6, replace=False)
-    assert _segment_local(ora, w, g, idx) < TOL
+    idx = np.random.default_rng(11).choice(w.n_ic, 64, replace=False)
+    worst = _segment_local(ora, w, g, idx)
+    print(f"config 2 full size: {idx.size} trajectories, {int(g['nseg'][idx].sum())} segments, worst segment-local "
+          f"error {worst:.2e}")
+    assert worst < TOL
 
 
 def test_edge_cases(pc, ora):

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2301_03989_gb300 import workloads as W
-from test_gpu_parity import TOL, rel_err
+from test_gpu_parity import TOL, pmap, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -52,29 +52,39 @@ def run_groups(pc, w, tf=None, **opts):
 
 
 def run_oracle_each(ora, w, tf=None):
+    """The oracle per trajectory (its own arc, degree and segment count), over
+    the host's cores."""
     m = ora.Model.from_workload(w.base)
     b = w.base
     tfv = w.tf if tf is None else tf
-    xf = np.zeros_like(w.x0)
-    st = np.zeros(w.n_ic, dtype=np.int32)
-    ns = np.zeros(w.n_ic, dtype=np.int32)
-    for i in range(w.n_ic):
+
+    def one(i):
         o = ora.Opts(N=int(w.N[i]), segments=int(w.S[i]), seg_mode=0, tol=b.tol, max_iters=b.max_iters,
                      max_depth=b.max_depth)
         r = ora.propagate(m, o, w.x0[i:i + 1], float(w.t0[i]), float(tfv[i]))
-        xf[i], st[i], ns[i] = r["xf"][0], r["status"][0], r["nseg"][0]
-    return dict(xf=xf, status=st, nseg=ns)
+        return r["xf"][0], r["status"][0], r["nseg"][0]
+    res = pmap(one, range(w.n_ic))
+    return dict(xf=np.array([r[0] for r in res]), status=np.array([r[1] for r in res], dtype=np.int32),
+                nseg=np.array([r[2] for r in res], dtype=np.int32))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_uneven_groups_vs_oracle(pc, ora, precision):
-    w = W.config5(M=48, years_max=3.0)
+    """256 trajectories of the uneven workload: arcs of 0.5-10 years, all four
+    degrees (32, 64, 128, 256), 4-80 base segments each."""
+    w = W.config5(M=256)
+    assert set(int(n) for n in w.N) == {32, 64, 128, 256}
+    assert w.tf.max() - w.t0.min() > 9 * W.YEAR and (w.tf - w.t0).min() < W.YEAR
     prec = pc.PC_PREC_MIXED if precision == "mixed" else pc.PC_PREC_FP64
     g = run_groups(pc, w, precision=prec)
     o = run_oracle_each(ora, w)
     assert g["code"] == pc.PC_OK
     np.testing.assert_array_equal(g["status"], o["status"])
     er, ev = rel_err(g["xf"], o["xf"])
+    for d in (32, 64, 128, 256):
+        k = w.N == d
+        print(f"config 5 {precision}, N = {d}: {int(k.sum())} trajectories, error vs oracle position max "
+              f"{er[k].max():.2e}, velocity max {ev[k].max():.2e}")
     assert er.max() < TOL and ev.max() < TOL, (er.max(), ev.max())
     assert (g["nseg"] != o["nseg"]).mean() <= 1 / 16
 
