@@ -286,11 +286,35 @@ def rel_errors(a, b):
     return er, ev
 
 
-def kernel_roofline(name, kt, steps, w, B, peaks):
+def split_flops_per_sweep(N: int) -> float:
+    """bf16 tensor-core flops of one trajectory-sweep of the split-digit
+    contraction: 28 digit-pair products over 16 ceil((N+1)/16) nodes, 8 ceil(N/8)
+    output nodes and 6 components, 2 flops each."""
+    return 28 * 2.0 * 16 * ((N + 16) // 16) * 8 * ((N + 7) // 8) * 6
+
+
+def bf16_peak_tflops():
+    """Measured dense bf16 peak (cuBLAS, sustained: the contraction runs inside
+    a long step); fallback 1.7 PFLOP/s."""
+    pk = _peaks()
+    v = pk.get("bf16_tflops_sustained")
+    return (v, "measured bf16 dense, sustained") if v else (1700.0, "fallback bf16 dense, sustained")
+
+
+def kernel_roofline(name, kt, steps, w, B, peaks, split=False):
     """Roofline of one kernel from the instrumented replay: algorithmic flops of
     the trajectory-sweeps it ran / its summed launch time."""
     launches, ms = kt[name]
-    if name == "contract":
+    extra = {}
+    if name == "contract" and split and w.N <= 255:
+        sweeps = kt["sweeps64"]
+        flops = split_flops_per_sweep(w.N) * sweeps
+        peak, src = peaks["bf16_tensor"]
+        bound, kern, dt = "tensor", "k_contract_split (exact 8-bit digit products, bf16 mma.sync m16n8k16)", "bf16"
+        if ms > 0:
+            extra["fp64_equivalent_tflops"] = contract_flops_per_sweep(w.N) * sweeps / (ms / 1000.0) / 1e12
+            extra["fp64_equivalent_frac_of_fp64_peak"] = extra["fp64_equivalent_tflops"] / peaks["fp64_tensor"][0]
+    elif name == "contract":
         flops = contract_flops_per_sweep(w.N) * kt["sweeps64"]
         peak, src = peaks["fp64_tensor"]
         bound, kern, dt = "tensor", "k_contract (FP64 DMMA mma.sync m16n8k4)", "f64"
@@ -304,13 +328,13 @@ def kernel_roofline(name, kt, steps, w, B, peaks):
         return None
     achieved = flops / (ms / 1000.0) / 1e12 if ms > 0 else 0.0
     tb = TRAFFIC_BYTES_PER_SWEEP.get(name)
-    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None,
-            "traffic": None if tb is None else tb * sweeps / max(1, launches),
-            "kernel": kern, "dtype": dt, "peak_source": src, "launches": launches,
-            "avg_launch_us": 1000.0 * ms / max(1, launches),
-            "algorithmic_flops_per_launch": flops / max(1, launches),
-            "trajectory_sweeps_per_launch": sweeps / max(1, launches)}
+    return dict({"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak if peak else None,
+                 "traffic": None if tb is None else tb * sweeps / max(1, launches),
+                 "kernel": kern, "dtype": dt, "peak_source": src, "launches": launches,
+                 "avg_launch_us": 1000.0 * ms / max(1, launches),
+                 "algorithmic_flops_per_launch": flops / max(1, launches),
+                 "trajectory_sweeps_per_launch": sweeps / max(1, launches)}, **extra)
 
 
 def run_ours(args, world, rank, local):
@@ -334,8 +358,9 @@ def run_ours(args, world, rank, local):
     switch_tol = args.switch_tol if args.switch_tol is not None else (1e-6 if args.workload == "precision" else 0.0)
     torch.cuda.synchronize(dev)
     t_plan = time.perf_counter()
+    contraction = pc.PC_CONTRACT_SPLIT if args.contraction == "split" else pc.PC_CONTRACT_DMMA
     plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED if mixed else pc.PC_PREC_FP64,
-                                 switch_tol=switch_tol)
+                                 switch_tol=switch_tol, contraction=contraction)
     torch.cuda.synchronize(dev)
     plan_ms = 1000.0 * (time.perf_counter() - t_plan)   # operator build + uploads, reported apart
     stream = torch.cuda.Stream(device=dev)
@@ -389,7 +414,7 @@ def run_ours(args, world, rank, local):
         # replay, no instrumentation; then a separate instrumented replay
         plain = None
         if mixed and not args.no_plain:
-            plan64 = pc.plan_from_workload(w, precision=pc.PC_PREC_FP64)
+            plan64 = pc.plan_from_workload(w, precision=pc.PC_PREC_FP64, contraction=contraction)
             xf64 = torch.zeros_like(x0)
             st64 = torch.zeros_like(st)
             it64 = torch.zeros_like(it)
@@ -417,10 +442,12 @@ def run_ours(args, world, rank, local):
 
     # roofline of the dominant kernel (by time in the instrumented replay)
     names = pc.KERNEL_NAMES
-    peaks = {"fp64_tensor": fp64_tensor_peak_tflops(), "fp32_alu": fp32_alu_peak_tflops()}
+    peaks = {"fp64_tensor": fp64_tensor_peak_tflops(), "fp32_alu": fp32_alu_peak_tflops(),
+             "bf16_tensor": bf16_peak_tflops()}
     tsum = sum(ktimes[k][1] for k in names)
     kname = max(names, key=lambda k: ktimes[k][1])
-    by_kernel = {k: kernel_roofline(k, ktimes, args.prof_steps, w, nB, peaks) for k in ("contract", "fp32")}
+    by_kernel = {k: kernel_roofline(k, ktimes, args.prof_steps, w, nB, peaks, split=args.contraction == "split")
+                 for k in ("contract", "fp32")}
     roof = by_kernel.get(kname) or by_kernel["contract"]
     roof = dict(roof, dominant_by_time=kname,
                 kernel_share={k: ktimes[k][1] / max(1e-9, tsum) for k in names},
@@ -472,6 +499,8 @@ def run_ours(args, world, rank, local):
                        "path": ("mixed FP32->FP64 batched sweep" if mixed else "plain FP64 batched sweep")
                                + " (per-trajectory segments, compaction, DMMA contraction)",
                        "switch_tol": switch_tol if mixed else None,
+                       "fp64_contraction": ("exact 8-bit digit products on the bf16 tensor cores"
+                                            if args.contraction == "split" else "FP64 tensor cores (DMMA)"),
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}",
                        "tuning": tuning},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx0.numel() * 8),
@@ -626,6 +655,8 @@ def main(argv=None):
     ap.add_argument("--switch-tol", type=float, default=None,
                     help="FP32 -> FP64 switch threshold (default 1e-6 precision, 0 flyby: when the FP32 change "
                          "stops falling)")
+    ap.add_argument("--contraction", choices=["split", "dmma"], default="split",
+                    help="FP64 contraction: exact digit products on the bf16 tensor cores, or the FP64 tensor cores")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--prof-steps", type=int, default=2, help="steps of the instrumented per-kernel replay")
     ap.add_argument("--workload", choices=["precision", "flyby", "uneven", "adjoint"], default="precision",

@@ -95,6 +95,14 @@ typedef struct {
                             to tol, with FP32 correction solves between them (refine32); not in
                             the paper: an extension; needs N <= 287 */
 
+#define PC_CONTRACT_DMMA 0   /* FP64 operator contraction on the FP64 tensor cores (mma.sync .f64) */
+#define PC_CONTRACT_SPLIT 1  /* the same contraction as exact products of 8-bit digits on the bf16
+                                tensor cores: each operand is cut into 7 signed digits (55 bits) against
+                                its row's or column's largest exponent, the digit products of one
+                                anti-diagonal are summed exactly in FP32, and the sums are combined in
+                                64-bit integers and FP64; error below that of an FP64 dot product
+                                (N <= 255; larger N use the FP64 tensor cores).  Not in the paper. */
+
 typedef struct {
   double tol;          /* stopping tolerance on the sweep-to-sweep change (overridden per call) */
   int relative;        /* 1: change relative to |r| and |v| of the new iterate; 0: absolute */
@@ -114,11 +122,13 @@ typedef struct {
   int refine32;        /* mixed precision: 1 lets an FP64 sweep whose change is below 1e-3 be
                           followed by an FP32 solve for the correction to its iterate (up to
                           two per segment attempt) instead of further FP64 sweeps */
+  int contraction;     /* PC_CONTRACT_DMMA or PC_CONTRACT_SPLIT: how FP64 sweeps apply the operator */
 } pc_options;
 
 /* Fills *o with the defaults: tol 1e-13, relative 1, max_iters 60, max_depth 8,
  * warm_start 1, seg_mode 0, truncated 0, stall_sweeps 5, stall_factor 1e3,
- * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0, refine32 1.
+ * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0, refine32 1,
+ * contraction PC_CONTRACT_DMMA.
  * Returns PC_EINVAL if o is NULL. */
 pc_status pc_options_default(pc_options *o);
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <vector>
 
 #include "pc.h"
@@ -20,6 +21,36 @@ constexpr int kMaxNpl = 9;   // mixed precision: N + 1 <= 32 * kMaxNpl (N <= 287
 // then one (r - r_b, mu_b/|r - r_b|^3) per body from float 16.  Shared by the
 // allocation and the kernels.
 __host__ __device__ constexpr int x32_stride(int B) { return 16 + 4 * B; }
+
+// Split-digit FP64 contraction (PC_CONTRACT_SPLIT).  A value v of a column
+// (or operator row) whose largest biased exponent is Bc is written as
+// v = 2^(Bc - 1021) sum_{a=1..7} d_a 2^(-8a) with integer digits |d_a| <= 128
+// (balanced base 256, the last one rounded to nearest): the 53-bit mantissa
+// shifted to 55 bits of fixed point, then cut into bytes from the bottom.  A
+// digit is exact in bf16, a product of two in FP32, and the sum over up to 129
+// nodes of the products on one anti-diagonal a + b = d (at most 7 of them)
+// stays below 2^24, so the bf16 tensor cores add them without rounding.
+constexpr int kSplitDigits = 7;
+__host__ __device__ inline void split_digits7(double v, int Bc, int d[kSplitDigits]) {
+  unsigned long long b;
+  memcpy(&b, &v, sizeof(b));
+  const int be = (int)((b >> 52) & 0x7ff);
+  long long M = 0;
+  if (be != 0 && be != 0x7ff) {
+    const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
+    const int sh = Bc - be - 2;  // >= -2 since be <= Bc: M < 2^55
+    if (sh <= 0) M = (long long)(m << (-sh));
+    else if (sh < 63) M = (long long)((m + (1ULL << (sh - 1))) >> sh);
+    if (b >> 63) M = -M;
+  }
+  for (int a = kSplitDigits - 1; a >= 1; a--) {
+    int r = (int)(M & 255);
+    if (r >= 128) r -= 256;
+    d[a] = r;
+    M = (M - r) >> 8;
+  }
+  d[0] = (int)M;
+}
 
 // Trajectory phases: FP64 sweeps, finished, FP32 sweeps (mixed precision).
 // PH_READY64: the FP32 phase ended in this round's k_fp32; the control kernel
@@ -171,6 +202,12 @@ struct pc_plan {
   float *d_K32T = nullptr;   // the operator rounded to FP32 and transposed, [N+1][32 npl]
   int npl = 0;               // ceil((N+1)/32): K32T rows are 32 npl floats long (0: no mixed path)
   float *d_K32R = nullptr;   // tiled FP32 kernels: [N+1][rows32], K32R[k][r] = K[r+1][k], zero-padded
+  // split-digit contraction: the operator rows' digits (rows = nodes 1..N) as
+  // bf16 mma B fragments [n_nt][n_ks][7 digits][32 lanes] x 2 words, and each
+  // row's largest biased exponent
+  unsigned *d_Kdig = nullptr;
+  int *d_Kexp = nullptr;
+  int split_nt = 0, split_ks = 0;   // ceil(N/8) node tiles, ceil((N+1)/16) k-steps
   int rows32 = 0;            // 32 ceil(N/32)
   double *d_tau = nullptr;   // [n]
   double *h_K = nullptr;     // host copy, (N+1) x (N+1)
@@ -229,4 +266,11 @@ cudaError_t launch_eval_warm(const pc_plan *plan, long long n_pts, const double 
                              cudaStream_t st);
 cudaError_t launch_apply_operator(const pc_plan *plan, long long n_ic, int ld, const double *x0, const double *G,
                                   double *Y, cudaStream_t st);
+// pc_split.cu: the FP64 contraction by exact digit products on the bf16 tensor
+// cores, over the round's FP64 list (diag = 0: Y' = x0 + K G with the change
+// and the residual) or over columns 0..n_ic-1 (diag = 1: Y' only).
+cudaError_t launch_contract_split(const pc_plan *plan, const Sweep &s, const Ctl &c, const double *G,
+                                  const double *Yold, double *Ynew, float *R32, int diag, cudaStream_t st);
+cudaError_t prepare_split(const pc_plan *plan);
+bool split_supported(const pc_plan *plan);
 }  // namespace pcx

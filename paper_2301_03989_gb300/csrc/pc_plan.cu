@@ -1,5 +1,6 @@
 // Plan creation: operator construction (host, extended precision), model
 // upload, workspace management, status strings.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -85,6 +86,7 @@ extern "C" pc_status pc_options_default(pc_options *o) {
   o->switch_tol = 0.0;
   o->max_rounds = 0;
   o->refine32 = 1;
+  o->contraction = PC_CONTRACT_DMMA;
   return PC_OK;
 }
 
@@ -92,7 +94,8 @@ static pc_status check_options(const pc_options &o) {
   if (!(o.tol >= 0.0) || o.max_iters < 1 || o.max_depth < 0 || o.max_depth > 30 || o.stall_sweeps < 1 ||
       !(o.stall_factor >= 0.0) || !(o.div_limit > 0.0) || (o.seg_mode != 0 && o.seg_mode != 1) ||
       (o.precision != PC_PREC_FP64 && o.precision != PC_PREC_MIXED) || o.max_rounds < 0 ||
-      !(o.switch_tol >= 0.0) || (o.refine32 != 0 && o.refine32 != 1))
+      !(o.switch_tol >= 0.0) || (o.refine32 != 0 && o.refine32 != 1) ||
+      (o.contraction != PC_CONTRACT_DMMA && o.contraction != PC_CONTRACT_SPLIT))
     return PC_EINVAL;
   return PC_OK;
 }
@@ -159,6 +162,53 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
       for (int r = 0; r < N; r++) Kr[(size_t)k * p->rows32 + r] = (float)p->h_K[(size_t)(r + 1) * n + k];
     if (e == cudaSuccess) e = dalloc(&p->d_K32R, Kr.size());
     if (e == cudaSuccess) e = cudaMemcpy(p->d_K32R, Kr.data(), sizeof(float) * Kr.size(), cudaMemcpyHostToDevice);
+  }
+  // Split-digit contraction: each operator row (node r+1) cut into 7 digits
+  // against its largest exponent, packed as bf16 mma B fragments (B[k][n] =
+  // K[node n][k]; lane (g, t) holds k = 2t, 2t+1 and 2t+8, 2t+9 of node g)
+  if (N <= 255) {
+    p->split_nt = (N + 7) / 8;
+    p->split_ks = (n + 15) / 16;
+    std::vector<int> kexp(N, 0), dig((size_t)N * kSplitDigits * p->split_ks * 16, 0);
+    for (int r = 0; r < N; r++) {
+      const double *row = p->h_K + (size_t)(r + 1) * n;
+      int bmax = 0;
+      for (int k = 0; k < n; k++) {
+        unsigned long long b;
+        std::memcpy(&b, row + k, sizeof(b));
+        bmax = std::max(bmax, (int)((b >> 52) & 0x7ff));
+      }
+      kexp[r] = bmax;
+      for (int k = 0; k < n; k++) {
+        int d[kSplitDigits];
+        split_digits7(row[k], bmax, d);
+        for (int a = 0; a < kSplitDigits; a++) dig[((size_t)r * kSplitDigits + a) * p->split_ks * 16 + k] = d[a];
+      }
+    }
+    auto bf16_bits = [](int v) -> unsigned {
+      const float f = (float)v;  // |v| <= 128: exact, and so is its bf16 (the top 16 bits)
+      unsigned u;
+      std::memcpy(&u, &f, sizeof(u));
+      return u >> 16;
+    };
+    auto digit = [&](int r, int a, int k) -> int {
+      return (r < N && k < n) ? dig[((size_t)r * kSplitDigits + a) * p->split_ks * 16 + k] : 0;
+    };
+    std::vector<unsigned> frag((size_t)p->split_nt * p->split_ks * kSplitDigits * 32 * 2);
+    for (int nt = 0; nt < p->split_nt; nt++)
+      for (int ks = 0; ks < p->split_ks; ks++)
+        for (int a = 0; a < kSplitDigits; a++)
+          for (int lane = 0; lane < 32; lane++) {
+            const int g = lane >> 2, t = lane & 3, r = nt * 8 + g, k0 = ks * 16 + 2 * t;
+            unsigned *f = frag.data() + ((((size_t)nt * p->split_ks + ks) * kSplitDigits + a) * 32 + lane) * 2;
+            f[0] = bf16_bits(digit(r, a, k0)) | (bf16_bits(digit(r, a, k0 + 1)) << 16);
+            f[1] = bf16_bits(digit(r, a, k0 + 8)) | (bf16_bits(digit(r, a, k0 + 9)) << 16);
+          }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_Kdig, sizeof(unsigned) * frag.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_Kdig, frag.data(), sizeof(unsigned) * frag.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_Kexp, sizeof(int) * N);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_Kexp, kexp.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
   }
   // Adjoint operator: K transposed without its zero row 0, KTp[j][k'] = K[k'+1][j].
   p->adj_mpad = (n + 15) / 16 * 16;
@@ -326,6 +376,8 @@ extern "C" void pc_plan_destroy(pc_plan *p) {
   cudaFree(p->d_KTp);
   cudaFree(p->d_K32T);
   cudaFree(p->d_K32R);
+  cudaFree(p->d_Kdig);
+  cudaFree(p->d_Kexp);
   cudaFree(p->d_tau);
   cudaFree(p->d_mu);
   cudaFree(p->d_mu32);

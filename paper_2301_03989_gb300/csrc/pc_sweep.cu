@@ -1523,6 +1523,10 @@ Mix live_mix(const pc_plan *p) {
   return mx;
 }
 
+// FP64 sweeps contract with the split-digit kernel when the plan asks for it
+// and its operator digits exist (N <= 255).
+bool use_split(const pc_plan *p) { return p->opt.contraction == PC_CONTRACT_SPLIT && split_supported(p); }
+
 unsigned sm_ctas(const pc_plan *p, int per_sm) { return (unsigned)((p->num_sms > 0 ? p->num_sms : 152) * per_sm); }
 
 size_t fp32_smem_bytes(const pc_plan *p) {
@@ -1602,6 +1606,10 @@ void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn,
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t prepare_launches(const pc_plan *p) {
+  if (use_split(p)) {
+    const cudaError_t e = prepare_split(p);
+    if (e != cudaSuccess) return e;
+  }
   if (!p->npl) return cudaSuccess;
   const int bytes = (int)fp32_smem_bytes(p);
   cudaError_t e = cudaFuncSetAttribute(k_fp32<FP32_KEPLER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1667,10 +1675,17 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   k_force<<<dim3(blocks_for(s.A, 32), (s.n + kForceNodes - 1) / kForceNodes), dim3(32, kForceNodes), 0, st>>>(
       s, c, p->model, Yc, E, Ai, w.G, p->d_tau, w.tails);
   if (ev) cudaEventRecord(ev[3], st);
-  // persistent FP64 contraction: contract_ctas_per_sm CTAs of kSplit warps per SM
-  const long long tiles = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
-  const long long blocks = std::max<long long>(1, std::min<long long>(sm_ctas(p, p->tune.contract_ctas_per_sm), tiles));
-  k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn, R32);
+  if (use_split(p)) {
+    // exact digit products on the bf16 tensor cores
+    e = launch_contract_split(p, s, c, w.G, Yc, Yn, R32, 0, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    // persistent FP64 contraction: contract_ctas_per_sm CTAs of kSplit warps per SM
+    const long long tiles = (long long)(s.rows_pad / 16) * ((s.A + 7) / 8);
+    const long long blocks =
+        std::max<long long>(1, std::min<long long>(sm_ctas(p, p->tune.contract_ctas_per_sm), tiles));
+    k_contract<<<(unsigned)blocks, 32 * kSplit, 0, st>>>(s, c, p->d_K, w.G, Yc, Yn, R32);
+  }
   if (branches) {
     e = cudaStreamWaitEvent(st, p->branch_ev[1], 0);
     if (e != cudaSuccess) return e;
@@ -1743,6 +1758,11 @@ cudaError_t launch_apply_operator(const pc_plan *p, long long n_ic, int ld, cons
   s.ld = ld;
   Ctl c = w.ctl[w.live];
   c.x = const_cast<double *>(x0);
+  if (use_split(p)) {
+    const cudaError_t e = prepare_split(p);
+    if (e != cudaSuccess) return e;
+    return launch_contract_split(p, s, c, G, nullptr, Y, nullptr, 1, st);
+  }
   const long long tiles = (long long)(s.rows_pad / 16) * ((n_ic + 7) / 8);
   k_contract_diag<<<(unsigned)std::min<long long>(tiles, sm_ctas(p, 8)), 32 * kSplit, 0, st>>>(s, c, p->d_K, G, Y);
   return cudaGetLastError();

@@ -21,6 +21,7 @@ _lib = None
 PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOTCONV, PC_ENONFINITE = 0, 1, 2, 3, 4, 5
 PC_IC_STALLED, PC_IC_UNRESOLVED, PC_IC_NOT_CONVERGED, PC_IC_NONFINITE, PC_IC_OUT_OF_RANGE = 1, 2, 4, 8, 16
 PC_PREC_FP64, PC_PREC_MIXED = 0, 1
+PC_CONTRACT_DMMA, PC_CONTRACT_SPLIT = 0, 1
 
 EXPORTS = ["pc_options_default", "pc_plan_create", "pc_propagate", "pc_propagate_ex", "pc_eval_ephemeris",
            "pc_eval_dynamics", "pc_eval_warm_start", "pc_apply_operator", "pc_plan_operator", "pc_plan_destroy",
@@ -65,7 +66,7 @@ class Options(C.Structure):
                 ("warm_start", C.c_int), ("seg_mode", C.c_int), ("truncated", C.c_int), ("stall_sweeps", C.c_int),
                 ("stall_factor", C.c_double), ("div_limit", C.c_double), ("trunc_tol", C.c_double),
                 ("precision", C.c_int), ("switch_tol", C.c_double), ("max_rounds", C.c_longlong),
-                ("refine32", C.c_int)]
+                ("refine32", C.c_int), ("contraction", C.c_int)]
 
 
 def lib():

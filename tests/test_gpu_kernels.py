@@ -37,14 +37,18 @@ def test_operator_matches_oracle(pc, ora, N, truncated):
     plan.close()
 
 
-@pytest.mark.parametrize("N", [16, 64, 128, 256])
+@pytest.mark.parametrize("contraction", ["dmma", "split"])
+@pytest.mark.parametrize("N", [16, 64, 128, 255, 256])
 @pytest.mark.parametrize("M", [1, 3, 33, 1000])
-def test_contraction_dmma_vs_oracle_operator(pc, ora, N, M):
-    """The DMMA contraction y = x0 + K g against the oracle's K applied in FP64
-    (numpy matmul), several row tiles, column tiles and a ragged tail."""
+def test_contraction_vs_oracle_operator(pc, ora, N, M, contraction):
+    """The contraction y = x0 + K g (FP64 tensor cores, or exact digit products
+    on the bf16 tensor cores; N = 256 has no digit operator and takes the FP64
+    path) against the oracle's K applied in FP64 (numpy matmul): several node
+    tiles, column tiles and a ragged tail."""
     import torch
     rng = np.random.default_rng(N * 1000 + M)
-    plan = pc.plan_create(N, 4, W.MU_SUN, [])
+    mode = pc.PC_CONTRACT_SPLIT if contraction == "split" else pc.PC_CONTRACT_DMMA
+    plan = pc.plan_create(N, 4, W.MU_SUN, [], options=pc.options_default(contraction=mode))
     x0 = rng.standard_normal((6, M)) * 1e8
     g = rng.standard_normal((N + 1, 6, M)) * 1e6
     y = torch.zeros((N + 1, 6, M), dtype=torch.float64, device="cuda")
@@ -56,6 +60,39 @@ def test_contraction_dmma_vs_oracle_operator(pc, ora, N, M):
     scale = np.abs(K).sum(1).max() * np.abs(g).max() + np.abs(x0).max()
     np.testing.assert_allclose(y.cpu().numpy(), ref, rtol=0, atol=4e-16 * scale)
     np.testing.assert_array_equal(y.cpu().numpy()[0], x0)
+    plan.close()
+
+
+def test_split_contraction_edge_cases(pc, ora):
+    """Digit contraction: columns of very different scale in one tile (each is
+    cut against its own exponent), an all-zero column, subnormal and tiny
+    entries next to large ones, and a NaN or an inf in one trajectory's
+    columns, which must reach every node of that trajectory and no other."""
+    import torch
+    N, M = 128, 21
+    rng = np.random.default_rng(3)
+    plan = pc.plan_create(N, 4, W.MU_SUN, [], options=pc.options_default(contraction=pc.PC_CONTRACT_SPLIT))
+    x0 = rng.standard_normal((6, M)) * 1e8
+    g = rng.standard_normal((N + 1, 6, M)) * (10.0 ** rng.integers(-30, 30, size=(1, 6, M)))
+    g[:, 2, 4] = 0.0
+    g[5, 1, 6] = 5e-320
+    g[7, 0, 6] = 1e-300
+    g[11, 3, 9] = np.nan
+    g[13, 5, 17] = np.inf
+    y = torch.zeros((N + 1, 6, M), dtype=torch.float64, device="cuda")
+    pc.apply_operator(plan, _dev(x0), _dev(g), y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    K = ora.pc_operator(N)
+    ok = np.ones(M, dtype=bool)
+    ok[[9, 17]] = False
+    assert np.isnan(got[1:, :, ~ok]).all()
+    np.testing.assert_array_equal(got[0], x0)
+    ld = np.longdouble
+    ref = (x0[None, :, ok].astype(ld) + np.einsum("jk,kcm->jcm", K.astype(ld), g[:, :, ok].astype(ld))).astype(float)
+    # per column: a few ulps of sum |K| times the column's own largest |g|
+    scale = np.abs(K).sum(1).max() * np.abs(g[:, :, ok]).max(0)[None] + np.abs(x0[None, :, ok])
+    assert (np.abs(got[:, :, ok] - ref) <= 4e-16 * scale).all()
     plan.close()
 
 
