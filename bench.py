@@ -52,7 +52,9 @@ IC_PER_RANK = {"precision": 65536, "flyby": 4096}
 # capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum over the
 # captured launches / their trajectory-sweeps); None until taken on the current
 # kernel.  A line's traffic is this figure times the launch's sweeps.
-TRAFFIC_BYTES_PER_SWEEP = {"contract": None, "fp32": None}
+# contract: k_contract_split on config 3 with 16,384 trajectories, 322 MB over
+# 7,460 trajectory-sweeps.
+TRAFFIC_BYTES_PER_SWEEP = {"contract": 43_200, "fp32": None}
 
 
 def _peaks():
@@ -306,6 +308,7 @@ def kernel_roofline(name, kt, steps, w, B, peaks, split=False):
     the trajectory-sweeps it ran / its summed launch time."""
     launches, ms = kt[name]
     extra = {}
+    tb_key = name
     if name == "contract" and split and w.N <= 255:
         sweeps = kt["sweeps64"]
         flops = split_flops_per_sweep(w.N) * sweeps
@@ -315,6 +318,7 @@ def kernel_roofline(name, kt, steps, w, B, peaks, split=False):
             extra["fp64_equivalent_tflops"] = contract_flops_per_sweep(w.N) * sweeps / (ms / 1000.0) / 1e12
             extra["fp64_equivalent_frac_of_fp64_peak"] = extra["fp64_equivalent_tflops"] / peaks["fp64_tensor"][0]
     elif name == "contract":
+        tb_key = None                       # no capture of the DMMA kernel in this build
         flops = contract_flops_per_sweep(w.N) * kt["sweeps64"]
         peak, src = peaks["fp64_tensor"]
         bound, kern, dt = "tensor", "k_contract (FP64 DMMA mma.sync m16n8k4)", "f64"
@@ -327,7 +331,7 @@ def kernel_roofline(name, kt, steps, w, B, peaks, split=False):
     else:
         return None
     achieved = flops / (ms / 1000.0) / 1e12 if ms > 0 else 0.0
-    tb = TRAFFIC_BYTES_PER_SWEEP.get(name)
+    tb = TRAFFIC_BYTES_PER_SWEEP.get(tb_key) if tb_key else None
     return dict({"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak if peak else None,
                  "traffic": None if tb is None else tb * sweeps / max(1, launches),

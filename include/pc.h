@@ -128,7 +128,7 @@ typedef struct {
 /* Fills *o with the defaults: tol 1e-13, relative 1, max_iters 60, max_depth 8,
  * warm_start 1, seg_mode 0, truncated 0, stall_sweeps 5, stall_factor 1e3,
  * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0, refine32 1,
- * contraction PC_CONTRACT_DMMA.
+ * contraction PC_CONTRACT_SPLIT.
  * Returns PC_EINVAL if o is NULL. */
 pc_status pc_options_default(pc_options *o);
 

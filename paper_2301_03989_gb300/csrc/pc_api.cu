@@ -1,6 +1,7 @@
 // Host driver of the batched sweep and the kernel-level entry points.
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "pc_internal.h"
@@ -100,6 +101,9 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   s.lc_cnt = w.ints + 8;
   s.tile_ctr = w.ints + 7;
   s.fp32_ctr = w.ints + 10;
+  s.kep_stride = p->kep_stride;
+  s.Lint = p->d_Lint;
+  s.YK17 = w.YK17;
   s.cnt64 = w.cnt64;
   s.list_cur = 0;
   s.A = (int)n_ic;
@@ -518,37 +522,42 @@ extern "C" pc_status pc_plan_autotune(pc_plan *p, long long n_ic, const double *
   if (ps == PC_OK) ps = trial(cur, &cur_ms);  // warm-up: workspace allocation, first captures
   if (ps == PC_OK) ps = trial(cur, &cur_ms);
   const bool mixed = p->opt.precision == PC_PREC_MIXED;
-  struct Axis {
-    int pc_tuning::*field;
-    std::vector<int> values;
+  // Coordinate descent over single fields, plus joint moves where one field's
+  // best value depends on another's (the one-trajectory FP32 kernel wants
+  // several CTAs per SM, the tiled one about one).
+  struct Move {
+    std::vector<std::pair<int pc_tuning::*, int>> set;
   };
-  const std::vector<Axis> axes = {
-      {&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8, 12, 16}},
-      {&pc_tuning::setup_ctas_per_sm, {2, 4, 8, 16}},
-      // FP32 kernels: one trajectory per CTA wins on short lists (its sweeps
-      // have the shortest latency), the tiled kernel on long ones
-      {&pc_tuning::fp32_rows, mixed ? std::vector<int>{4, 8} : std::vector<int>{}},
-      {&pc_tuning::fp32_slots, mixed ? std::vector<int>{8, 16, 32} : std::vector<int>{}},
-      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{}},
-      {&pc_tuning::fp32_rows, mixed ? std::vector<int>{0} : std::vector<int>{}},
-      {&pc_tuning::fp32_ctas_per_sm, mixed ? std::vector<int>{4, 6, 8, 12} : std::vector<int>{}},
-      {&pc_tuning::side_priority, mixed ? std::vector<int>{0, 1} : std::vector<int>{}},
-      {&pc_tuning::rounds_per_batch, {4, 8, 16, 32}},
-      {&pc_tuning::repack_div, {4, 8, 16}},
-      {&pc_tuning::graphs, {0, 1}},
+  std::vector<Move> moves;
+  auto axis = [&](int pc_tuning::*f, std::initializer_list<int> vals) {
+    for (int v : vals) moves.push_back(Move{{{f, v}}});
   };
-  for (const Axis &ax : axes) {
-    for (int v : ax.values) {
-      if (ps != PC_OK) break;
-      if (cur.*(ax.field) == v) continue;
-      pc_tuning cand = cur;
-      cand.*(ax.field) = v;
-      double ms = 0.0;
-      ps = trial(cand, &ms);
-      if (ps == PC_OK && ms < 0.99 * cur_ms) {  // keep a change only for a clear gain
-        cur = cand;
-        cur_ms = ms;
-      }
+  axis(&pc_tuning::contract_ctas_per_sm, {2, 3, 4, 6, 8, 12, 16});
+  axis(&pc_tuning::setup_ctas_per_sm, {2, 4, 8, 16});
+  if (mixed) {
+    for (int r : {0, 4, 8})
+      for (int c : (r == 0 ? std::vector<int>{4, 6, 8, 12} : std::vector<int>{1, 2}))
+        moves.push_back(Move{{{&pc_tuning::fp32_rows, r}, {&pc_tuning::fp32_ctas_per_sm, c}}});
+    axis(&pc_tuning::fp32_slots, {8, 16, 32});
+    axis(&pc_tuning::side_priority, {0, 1});
+  }
+  axis(&pc_tuning::rounds_per_batch, {4, 8, 16, 32});
+  axis(&pc_tuning::repack_div, {4, 8, 16});
+  axis(&pc_tuning::graphs, {0, 1});
+  for (const Move &mv : moves) {
+    if (ps != PC_OK) break;
+    pc_tuning cand = cur;
+    bool same = true;
+    for (const auto &fv : mv.set) {
+      same = same && cur.*(fv.first) == fv.second;
+      cand.*(fv.first) = fv.second;
+    }
+    if (same) continue;
+    double ms = 0.0;
+    ps = trial(cand, &ms);
+    if (ps == PC_OK && ms < 0.99 * cur_ms) {  // keep a change only for a clear gain
+      cur = cand;
+      cur_ms = ms;
     }
   }
   p->tune = cur;

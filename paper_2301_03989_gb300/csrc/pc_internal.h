@@ -95,8 +95,13 @@ constexpr int kCtlDoubles = 16 + kKeplerConsts;  // x[6] + t0, tf, total, sgn, h
 constexpr int kCtlInts = 12;     // 10 ints + err32 + ncorr
 
 // Sweep parameters of one call.
+constexpr int kKepNodes = 17;  // interpolation nodes of the warm start
+
 struct Sweep {
   int N, n, kpad, rows_pad;  // degree, nodes, padded k extent, padded output rows (nodes 1..N)
+  int kep_stride;            // warm start solved at nodes 0, kep_stride, ..., N (0: at every node)
+  const double *Lint;        // [n][17] interpolation weights (kep_stride > 0)
+  double *YK17;              // [17][6][ld] Kepler solutions at those nodes
   long long n_ic;
   int ld;                    // leading dimension over slots (multiple of 8)
   int A;                     // slots [0, A) may hold active trajectories
@@ -149,6 +154,7 @@ struct Workspace {
   double *Aind[2] = {nullptr, nullptr}; // [n][3][ld] summed indirect acceleration (+ repack target)
   // mixed precision (allocated when the plan asks for it), by new-segment list entry
   double *YK = nullptr;      // [entry][n][6] FP64 warm start
+  double *YK17 = nullptr;    // [17][6][ld] Kepler solutions at the interpolation nodes, by new-segment entry
   float *X32 = nullptr;      // [entry][n][x32_stride(B)] FP32 node records
   float *R32[2] = {nullptr, nullptr};   // [n][6][ld] FP64 sweep residual Y' - Y, rounded (+ repack target)
   Ctl ctl[2]{};              // live control state and repack target
@@ -205,6 +211,11 @@ struct pc_plan {
   // split-digit contraction: the operator rows' digits (rows = nodes 1..N) as
   // bf16 mma B fragments [n_nt][n_ks][7 digits][32 lanes] x 2 words, and each
   // row's largest biased exponent
+  // warm start: Kepler's equation solved at every kep_stride-th node (the 17
+  // nodes of the embedded degree-16 Chebyshev-Lobatto grid), the other nodes
+  // interpolated with d_Lint [N+1][17]; kep_stride 0: solved at every node
+  int kep_stride = 0;
+  double *d_Lint = nullptr;
   unsigned *d_Kdig = nullptr;
   int *d_Kexp = nullptr;
   int split_nt = 0, split_ks = 0;   // ceil(N/8) node tiles, ceil((N+1)/16) k-steps

@@ -86,7 +86,7 @@ extern "C" pc_status pc_options_default(pc_options *o) {
   o->switch_tol = 0.0;
   o->max_rounds = 0;
   o->refine32 = 1;
-  o->contraction = PC_CONTRACT_DMMA;
+  o->contraction = PC_CONTRACT_SPLIT;
   return PC_OK;
 }
 
@@ -162,6 +162,29 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
       for (int r = 0; r < N; r++) Kr[(size_t)k * p->rows32 + r] = (float)p->h_K[(size_t)(r + 1) * n + k];
     if (e == cudaSuccess) e = dalloc(&p->d_K32R, Kr.size());
     if (e == cudaSuccess) e = cudaMemcpy(p->d_K32R, Kr.data(), sizeof(float) * Kr.size(), cudaMemcpyHostToDevice);
+  }
+  // Warm-start interpolation: Lagrange weights of the 17 nodes tau_{i N/16}
+  // (Chebyshev-Lobatto nodes of degree 16) at every node, in long double;
+  // rows of the 17 nodes themselves are exact unit vectors.
+  if (N % 16 == 0 && N >= 32) {
+    p->kep_stride = N / 16;
+    std::vector<double> L((size_t)n * kKepNodes, 0.0);
+    for (int j = 0; j < n; j++) {
+      if (j % p->kep_stride == 0) {
+        L[(size_t)j * kKepNodes + j / p->kep_stride] = 1.0;
+        continue;
+      }
+      const long double x = (long double)p->h_tau[j];
+      for (int i = 0; i < kKepNodes; i++) {
+        const long double xi = (long double)p->h_tau[i * p->kep_stride];
+        long double l = 1.0L;
+        for (int k = 0; k < kKepNodes; k++)
+          if (k != i) l *= (x - (long double)p->h_tau[k * p->kep_stride]) / (xi - (long double)p->h_tau[k * p->kep_stride]);
+        L[(size_t)j * kKepNodes + i] = (double)l;
+      }
+    }
+    if (e == cudaSuccess) e = dalloc(&p->d_Lint, L.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_Lint, L.data(), sizeof(double) * L.size(), cudaMemcpyHostToDevice);
   }
   // Split-digit contraction: each operator row (node r+1) cut into 7 digits
   // against its largest exponent, packed as bf16 mma B fragments (B[k][n] =
@@ -317,6 +340,7 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic, int mixed) {
     if (e == cudaSuccess) e = dalloc(&w.X32, n * (size_t)x32_stride((int)B) * ld);
     for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc(&w.R32[b], n * 6 * ld);
   }
+  if (p->kep_stride > 0 && e == cudaSuccess) e = dalloc(&w.YK17, (size_t)kKepNodes * 6 * ld);
   if (e == cudaSuccess) e = dalloc(&w.lists, 6 * ld);
   if (e == cudaSuccess) e = dalloc(&w.pos, ld);
   if (e == cudaSuccess) e = dalloc(&w.cnt64, 2);
@@ -346,6 +370,7 @@ void pcx::free_workspace(pc_plan *p) {
     cudaFree(w.ctl_block[b]);
   }
   cudaFree(w.YK);
+  cudaFree(w.YK17);
   cudaFree(w.X32);
   for (int b = 0; b < 2; b++) cudaFree(w.R32[b]);
   cudaFree(w.G);
@@ -377,6 +402,7 @@ extern "C" void pc_plan_destroy(pc_plan *p) {
   cudaFree(p->d_K32T);
   cudaFree(p->d_K32R);
   cudaFree(p->d_Kdig);
+  cudaFree(p->d_Lint);
   cudaFree(p->d_Kexp);
   cudaFree(p->d_tau);
   cudaFree(p->d_mu);

@@ -254,6 +254,50 @@ __device__ __forceinline__ void add_indirect(const Model &md, int b, const doubl
   for (int ax = 0; ax < 3; ax++) ind[ax] = fma(k, r[ax], ind[ax]);
 }
 
+// The warm start of a segment is interpolated from 17 nodes when the segment
+// spans at most 1.5 rad of mean anomaly (a degree-16 Chebyshev interpolant of
+// the Kepler arc is then exact to rounding); longer segments, and arcs with
+// no mean motion, are solved at every node.
+constexpr double kInterpMaxAnomaly = 1.5;
+__device__ __forceinline__ bool kepler_interpolated(const Sweep &s, const Ctl &c, int m) {
+  return s.kep_stride > 0 && fabs(c.kc[4 * s.ld + m] * (c.tb[m] - c.ta[m])) <= kInterpMaxAnomaly &&
+         c.kc[(size_t)0 * s.ld + m] > 0.0;
+}
+
+// Warm start of the new segments at the 17 interpolation nodes j = i *
+// kep_stride (grid-stride over list entries x those nodes, entries fastest):
+// Kepler's equation solved as at every node before, NaN where the iteration
+// does not settle (k_setup then starts the whole segment cold).  Node 0 is the
+// start state itself.
+__global__ void k_kepler17(Sweep s, Ctl c, const double *__restrict__ tau) {
+  const int cur = s.list_cur;
+  const long long count = s.list_cnt[cur];
+  const int *__restrict__ list = s.list[cur];
+  const long long total = count * kKepNodes;
+  const int ld = s.ld;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / count);
+    const long long e = i - (long long)k * count;
+    const int m = list[e];
+    if (!kepler_interpolated(s, c, m)) continue;
+    const int j = k * s.kep_stride;
+    double x0[6], y[6];
+    for (int q = 0; q < 6; q++) x0[q] = c.x[q * ld + m];
+    bool ok = true;
+    if (j > 0) {
+      double kc[kKepConsts];
+      for (int q = 0; q < kKepConsts; q++) kc[q] = c.kc[q * ld + m];
+      const double t = dadd(c.w1[m], dmul(c.w2[m], tau[j]));
+      ok = kepler_solve(kc, x0, dsub(t, c.ta[m]), y);
+    } else {
+      for (int q = 0; q < 6; q++) y[q] = x0[q];
+    }
+    for (int q = 0; q < 6; q++)
+      s.YK17[((size_t)k * 6 + q) * ld + e] = ok ? y[q] : __longlong_as_double(0x7FF8000000000000LL);
+  }
+}
+
 // Mixed-precision inputs of the new segments, by list entry e (not slot):
 //   YK[e][j][6]        FP64 warm start y_K at node j
 //   X32[e][j][xs]      FP32 record of node j, in float4 groups:
@@ -294,9 +338,28 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     for (int q = 0; q < 6; q++) x0[q] = c.x[q * ld + m];
     bool ok = false;
     if (j > 0 && s.warm) {
-      double kc[kKepConsts];
-      for (int q = 0; q < kKepConsts; q++) kc[q] = c.kc[q * ld + m];
-      ok = kepler_solve(kc, x0, dsub(t, c.ta[m]), y);
+      if (kepler_interpolated(s, c, m)) {
+        // interpolated from the 17 solved nodes (exact at those nodes)
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        bool fin = true;
+        const double *Lj = s.Lint + (size_t)j * kKepNodes;
+        for (int k = 0; k < kKepNodes; k++) {
+          const double l = Lj[k];
+#pragma unroll
+          for (int q = 0; q < 6; q++) {
+            const double v = s.YK17[((size_t)k * 6 + q) * ld + e];
+            fin = fin && isfinite(v);
+            acc[q] = fma(l, v, acc[q]);
+          }
+        }
+        ok = fin;
+        if (ok)
+          for (int q = 0; q < 6; q++) y[q] = acc[q];
+      } else {
+        double kc[kKepConsts];
+        for (int q = 0; q < kKepConsts; q++) kc[q] = c.kc[q * ld + m];
+        ok = kepler_solve(kc, x0, dsub(t, c.ta[m]), y);
+      }
     }
     if (!ok)
       for (int q = 0; q < 6; q++) y[q] = x0[q];
@@ -1662,6 +1725,10 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[0], st);
+  if (s.warm && s.kep_stride > 0) {
+    k_kepler17<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->d_tau);
+    p->acc_launches += 1;
+  }
   k_setup<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
   if (ev) cudaEventRecord(ev[1], st);
   float *R32 = s.refine ? w.R32[w.live] : nullptr;

@@ -70,10 +70,13 @@ def rel_err(a, b):
     return er, ev
 
 
-def test_config1_full(pc, ora):
-    """Sun + Venus + Earth, 64 ICs, one revolution in 8 segments, N = 64, tol 1e-13."""
+@pytest.mark.parametrize("contraction", ["split", "dmma"])
+def test_config1_full(pc, ora, contraction):
+    """Sun + Venus + Earth, 64 ICs, one revolution in 8 segments, N = 64, tol
+    1e-13; both FP64 contractions (split digits on the bf16 tensor cores, the
+    default, and the FP64 tensor cores)."""
     w = W.config1()
-    g = run_gpu(pc, w, w.x0)
+    g = run_gpu(pc, w, w.x0, contraction=pc.PC_CONTRACT_SPLIT if contraction == "split" else pc.PC_CONTRACT_DMMA)
     o = run_oracle(ora, w, w.x0)
     assert g["code"] == pc.PC_OK
     er, ev = rel_err(g["xf"], o["xf"])
