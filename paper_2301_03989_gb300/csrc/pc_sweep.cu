@@ -727,41 +727,17 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
   const int count = MODE == FP32_KEPLER ? s.list_cnt[cur] : s.lc_cnt[cur];
   const int *list = MODE == FP32_KEPLER ? s.list[cur] : s.lc[cur];
   const int boff = MODE == FP32_KEPLER ? 3 : 4;  // float4 index of the first body record
-  const float muc = (float)md.mu_c;
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int m = list[e];
     const float w2f = (float)c.w2[m];
     const float4 *rc = reinterpret_cast<const float4 *>(Rs + (size_t)(node ? j : 0) * xss);
     const size_t yb = (size_t)j * 6 * ld + m;
-    if (MODE == FP32_KEPLER && node) {
-      // the node record written by the set-up kernel, to shared memory
+    if (node) {
+      // the node record written by the set-up kernel (k_setup for new segments,
+      // k_corr_setup for correction solves), to shared memory
       const float4 *src = reinterpret_cast<const float4 *>(mx.X32 + ((size_t)e * n + j) * mx.xs);
       float4 *dst = reinterpret_cast<float4 *>(Rs + (size_t)j * xss);
       for (int v = 0; v < mx.xs / 4; v++) dst[v] = src[v];
-    }
-    if (MODE == FP32_CORR && node) {
-      // node record from the FP64 iterate, its residual and the body positions
-      float4 *wc = reinterpret_cast<float4 *>(Rs + (size_t)j * xss);
-      double base[6];
-      float res[6];
-#pragma unroll
-      for (int q = 0; q < 6; q++) {
-        res[q] = (j == 0) ? 0.0f : R32[yb + (size_t)q * ld];
-        base[q] = Yc[yb + (size_t)q * ld] - (double)res[q];
-      }
-      const float bx = (float)base[0], by = (float)base[1], bz = (float)base[2];
-      const float ir = rsqrtf(bx * bx + by * by + bz * bz);
-      wc[0] = make_float4(bx, by, bz, muc * ir * ir * ir);
-      wc[1] = make_float4((float)base[3], (float)base[4], (float)base[5], 0.0f);
-      wc[2] = make_float4(res[0], res[1], res[2], res[3]);
-      wc[3] = make_float4(res[4], res[5], 0.0f, 0.0f);
-      for (int b = 0; b < B; b++) {
-        const double *eb = E + (size_t)(j * B + b) * 3 * ld + m;
-        const float dx = (float)(base[0] - eb[0]), dy = (float)(base[1] - eb[(size_t)ld]),
-                    dz = (float)(base[2] - eb[(size_t)2 * ld]);
-        const float id = rsqrtf(dx * dx + dy * dy + dz * dz);
-        wc[4 + b] = make_float4(dx, dy, dz, mu32[b] * id * id * id);
-      }
     }
     float dl[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acc[6];
     float res[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -1031,11 +1007,40 @@ __device__ __forceinline__ void fp32_corr_record(const Sweep &s, const Model &md
   }
 }
 
-// Shared-memory bytes of the tiled FP32 kernel: operator (when staged), force
-// table, reduction partials, GMs.
-__host__ __device__ inline size_t fp32t_smem_bytes(int n, int rows32, int T, int RG, bool ksm, int B) {
-  return sizeof(float) * ((ksm ? (size_t)n * rows32 : 0) + (size_t)n * 6 * T + 2 * (size_t)T * (RG / 4) + B + 4);
+// Correction-solve records: for every entry e of the round's correction list
+// and every node j, the record of fp32_corr_record in X32[e][j] (grid-stride
+// over entries x nodes, entries fastest, so neighbouring threads read
+// neighbouring slots of the FP64 arrays).  Runs after the new-segment FP32
+// kernel, which is done with X32, and before the correction solves.
+__global__ void k_corr_setup(Sweep s, Model md, const float *__restrict__ mu32, const double *__restrict__ Yc,
+                             const double *__restrict__ E, const float *__restrict__ R32, Mix mx) {
+  const int cur = s.list_cur;
+  const long long count = s.lc_cnt[cur];
+  const int *__restrict__ list = s.lc[cur];
+  const long long total = count * s.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / count);
+    const long long e = i - (long long)j * count;
+    fp32_corr_record(s, md, mu32, Yc, E, R32, j, list[e],
+                     reinterpret_cast<float4 *>(mx.X32 + ((size_t)e * s.n + j) * mx.xs));
+  }
 }
+
+// Shared-memory bytes of the tiled FP32 kernel: operator (when staged), force
+// table, node records of the slots, reduction partials, GMs.
+__host__ __device__ inline size_t fp32t_smem_bytes(int n, int rows32, int T, int RG, bool ksm, int B) {
+  const int xss = fp32_rec_stride(x32_stride(B));
+  return sizeof(float) * ((ksm ? (size_t)n * rows32 : 0) + (size_t)n * 6 * T + (size_t)T * n * xss +
+                          2 * (size_t)T * (RG / 4) + B + 4);
+}
+
+// 16-byte asynchronous copy global -> shared (no register staging).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
 template <int MODE, int R, bool KSM>
 __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
@@ -1050,7 +1055,9 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
   const int rg_hi = wid % RG4, rg = rg_hi * 4 + (lane & 3), t = (wid / RG4) * 8 + (lane >> 2);
   float *Ks = reinterpret_cast<float *>(fp32t_sm4);          // [n][rows32] when KSM
   float *Gs = Ks + (KSM ? (size_t)n * rows32 : 0);             // [n][T][6]
-  float *red = Gs + (size_t)n * 6 * T;                         // [2][T][RG4]
+  const int xs4 = mx.xs / 4, xss = fp32_rec_stride(mx.xs), xss4 = xss / 4;
+  float *Rs = Gs + (size_t)n * 6 * T;                          // [T][n][xss] node records of the slots
+  float *red = Rs + (size_t)T * n * xss;                       // [2][T][RG4]
   float *mus = red + 2 * T * RG4;                              // [B]
   const int cur = s.list_cur;
   const int count = MODE == FP32_KEPLER ? s.list_cnt[cur] : s.lc_cnt[cur];
@@ -1083,6 +1090,19 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
   int m = sl.m[t];
   float w2f = sl.w2[t];
   bool fresh = true;
+  // the slot's node records (written by the set-up kernels) to shared memory,
+  // once per trajectory, by the slot's threads
+  auto load_records = [&](int entry) {
+    const float4 *src = reinterpret_cast<const float4 *>(mx.X32) + (size_t)entry * n * xs4;
+    float4 *dst = reinterpret_cast<float4 *>(Rs) + (size_t)t * n * xss4;
+    for (int idx = rg; idx < n * xs4; idx += RG) {
+      const int j = idx / xs4, v = idx - j * xs4;
+      cp_async16(dst + (size_t)j * xss4 + v, src + idx);
+    }
+  };
+  if (e >= 0) load_records(e);
+  cp_async_wait_all();
+  __syncthreads();
   float dl[R][6], acc[R][6];
   for (;;) {
     const bool live = e >= 0;
@@ -1091,18 +1111,11 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       for (int i = 0; i < R; i++)
 #pragma unroll
         for (int q = 0; q < 6; q++) dl[i][q] = 0.0f;
-      if (MODE == FP32_CORR) {
-        // node records from the FP64 iterate, its residual and the body positions
-        float4 *rb = reinterpret_cast<float4 *>(mx.X32 + (size_t)e * n * mx.xs);
-        if (rg == 0) fp32_corr_record(s, md, mus, Yc, E, R32, 0, m, rb);
-        for (int i = 0; i < R; i++)
-          if (j0 + i <= N) fp32_corr_record(s, md, mus, Yc, E, R32, j0 + i, m, rb + (size_t)(j0 + i) * (mx.xs / 4));
-      }
     }
     fresh = false;
     // force rows of the thread's nodes
+    const float4 *rb = reinterpret_cast<const float4 *>(Rs) + (size_t)t * n * xss4;
     if (live) {
-      const float4 *rb = reinterpret_cast<const float4 *>(mx.X32 + (size_t)e * n * mx.xs);
       float g[6];
       if (rg == 0) {
         const float z[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -1116,7 +1129,7 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       for (int i = 0; i < R; i++) {
         const int j = j0 + i;
         if (j <= N) {
-          fp32_force_row<MODE>(rb + (size_t)j * (mx.xs / 4), B, mus, md.indirect, dl[i], w2f, g);
+          fp32_force_row<MODE>(rb + (size_t)j * xss4, B, mus, md.indirect, dl[i], w2f, g);
           float2 *gp = reinterpret_cast<float2 *>(Gs + ((size_t)j * T + t) * 6);
           gp[0] = make_float2(g[0], g[1]);
           gp[1] = make_float2(g[2], g[3]);
@@ -1157,12 +1170,11 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
         }
       }
       // change and size of the deviation, relative to the iterate
-      const float4 *rb = reinterpret_cast<const float4 *>(mx.X32 + (size_t)e * n * mx.xs);
 #pragma unroll
       for (int i = 0; i < R; i++) {
         const int j = j0 + i;
         if (j <= N) {
-          const float4 *rj = rb + (size_t)j * (mx.xs / 4);
+          const float4 *rj = rb + (size_t)j * xss4;
           const float4 rk = rj[0], vk = rj[1];
           const float yk[6] = {rk.x, rk.y, rk.z, vk.x, vk.y, vk.z};
           float res[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -1292,7 +1304,10 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       m = sl.m[t];
       w2f = sl.w2[t];
       fresh = true;
+      if (e >= 0) load_records(e);
     }
+    cp_async_wait_all();
+    __syncthreads();  // the new trajectories' records are in place
     if (!any) break;
   }
 }
@@ -1600,9 +1615,10 @@ size_t fp32_smem_bytes(const pc_plan *p) {
 
 // Launch shape of the tiled FP32 kernel under the plan's tuning: R rows per
 // thread, RG = 4 ceil(N / 4R) row groups, T slots (a multiple of 8, at most
-// 256 / RG threads' worth), the operator staged in shared memory when it fits.
-// ok = 0 when even 8 slots exceed 256 threads (N > 256): one trajectory per
-// CTA then.
+// 256 / RG threads' worth and as many as fit in shared memory with their
+// node records), the operator staged in shared memory when it fits.  ok = 0
+// when even 8 slots exceed 256 threads (N > 256) or shared memory: one
+// trajectory per CTA then.
 struct Fp32tShape {
   int R, RG, T, threads;
   bool ksm, ok;
@@ -1622,9 +1638,15 @@ Fp32tShape fp32t_shape(const pc_plan *p) {
   sh.ok = p->tune.fp32_rows != 0 && sh.RG * 8 <= kFp32tMaxThreads;
   const int tmax = std::min(kFp32tMaxSlots, std::max(8, kFp32tMaxThreads / sh.RG / 8 * 8));
   sh.T = std::max(8, std::min(p->tune.fp32_slots / 8 * 8, tmax));
+  // the largest slot count whose node records fit beside the staged operator;
+  // failing that 8 slots with the operator read through L1; failing that
+  // (many bodies) one trajectory per CTA
+  const int B = p->model.B;
+  while (sh.T > 8 && fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, true, B) > kMaxDynSmem) sh.T -= 8;
+  sh.ksm = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, true, B) <= kMaxDynSmem;
+  if (!sh.ksm && fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, false, B) > kMaxDynSmem) sh.ok = false;
   sh.threads = sh.RG * sh.T;
-  sh.ksm = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, true, p->model.B) <= kMaxDynSmem;
-  sh.smem = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, sh.ksm, p->model.B);
+  sh.smem = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, sh.ksm, B);
   return sh;
 }
 
@@ -1733,7 +1755,11 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   if (ev) cudaEventRecord(ev[1], st);
   float *R32 = s.refine ? w.R32[w.live] : nullptr;
   if (s.mixed) launch_fp32<FP32_KEPLER>(p, s, Yc, Yn, E, R32, mx, sb);
-  if (s.refine) launch_fp32<FP32_CORR>(p, s, Yc, Yn, E, R32, mx, sb);
+  if (s.refine) {
+    k_corr_setup<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, p->model, p->d_mu32, Yc, E, R32, mx);
+    p->acc_launches += 1;
+    launch_fp32<FP32_CORR>(p, s, Yc, Yn, E, R32, mx, sb);
+  }
   if (branches) {
     e = cudaEventRecord(p->branch_ev[1], sb);
     if (e != cudaSuccess) return e;

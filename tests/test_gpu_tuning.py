@@ -65,6 +65,29 @@ def test_tunings_and_graphs_are_bitwise_neutral(pc, precision):
     plan.close()
 
 
+def test_fp32_variants_are_bitwise_neutral_on_few_bodies(pc):
+    """Config 3 (Sun + Venus + Earth): the tiled FP32 kernel keeps its
+    trajectories' node records in shared memory (with many bodies they do not
+    fit and the one-trajectory-per-CTA kernel runs instead); every tile shape
+    and the one-trajectory-per-CTA kernel give bitwise the same results."""
+    import torch
+    w = W.config3(M=600)
+    plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED, switch_tol=1e-6)
+    x0d = torch.as_tensor(W.to_planar(w.x0), device="cuda")
+    tf = 0.3 * W.YEAR
+    pc.set_tuning(plan, fp32_rows=0, fp32_ctas_per_sm=4)
+    base = _run(pc, plan, w, x0d, tf)
+    assert base[0] == pc.PC_OK
+    for kw in (dict(fp32_rows=4, fp32_slots=8, fp32_ctas_per_sm=1), dict(fp32_rows=8, fp32_slots=8),
+               dict(fp32_rows=4, fp32_slots=64, fp32_ctas_per_sm=2), dict(fp32_rows=8, fp32_slots=16, graphs=0)):
+        pc.set_tuning(plan, **kw)
+        r = _run(pc, plan, w, x0d, tf)
+        for a, b in zip(base[2:], r[2:]):
+            assert torch.equal(a, b), kw
+        pc.set_tuning(plan, **DEFAULT_TUNING)
+    plan.close()
+
+
 def test_tuning_validation(pc):
     w = W.config1(M=8)
     plan = pc.plan_from_workload(w)
