@@ -55,7 +55,7 @@ class _Opts(C.Structure):
                 ("seg_mode", C.c_int), ("segments", C.c_int), ("stall_sweeps", C.c_int),
                 ("stall_factor", C.c_double), ("div_limit", C.c_double), ("trunc_tol", C.c_double),
                 ("dyn", C.c_int),
-                ("dyn_param", C.c_double * 3)]
+                ("dyn_param", C.c_double * 3), ("order", C.c_int)]
 
 
 class _StopState(C.Structure):
@@ -170,6 +170,7 @@ class Opts:
     trunc_tol: float = 1e-13
     dyn: int = DYN_NBODY
     dyn_param: tuple = (0.0, 0.0, 0.0)
+    order: int = 1
 
     def struct(self) -> _Opts:
         s = _Opts()
@@ -178,6 +179,7 @@ class Opts:
         s.seg_mode, s.segments, s.stall_sweeps = int(self.seg_mode), int(self.segments), int(self.stall_sweeps)
         s.stall_factor, s.div_limit, s.dyn = float(self.stall_factor), float(self.div_limit), int(self.dyn)
         s.trunc_tol = float(self.trunc_tol)
+        s.order = int(self.order)
         for i in range(3):
             s.dyn_param[i] = float(self.dyn_param[i])
         return s

@@ -43,6 +43,10 @@
  *   ora_pc2_segment      pinned: constant acceleration exact, harmonic
  *                                oscillator closed form, same fixed point as
  *                                ora_pc_segment on a flyby-free segment
+ *   order 2 of ora_pc_segment / ora_propagate
+ *                        pinned: bitwise ora_pc2_segment on a segment; same
+ *                                fixed point as order 1 end to end; Gauss-
+ *                                Legendre; fewer sweeps
  */
 #include <math.h>
 #include <pthread.h>
@@ -96,6 +100,7 @@ typedef struct {
   double trunc_tol;    /* resolution test on the Chebyshev tail (<= 0 disables) */
   int dyn;             /* ORA_DYN_* */
   double dyn_param[3]; /* constant acceleration vector, or omega^2 in [0] */
+  int order;           /* 1: the paper's sweep; 2: the second-order form (ora_pc2_segment) */
 } ora_opts;
 
 /* ------------------------------------------------------------------ */
@@ -424,6 +429,11 @@ int ora_stop_rule(const ora_opts *o, ora_stop_state *st, double e, int sweep) {
 
 /* ------------------------------------------------------------------ */
 /* One PC segment for one trajectory: the Picard iteration of Eq. (2) in */
+/* the matrix form of the paper (order 1), or its second-order form       */
+/* (order 2: V' = v0 + omega2 K A(Y), R' = r0 + omega2 K V'; the stop,    */
+/* stall and resolution rules are the same, the resolution test on the   */
+/* force table of the iterate the sweep started from).                   */
+/* Order 1: */
 /* the matrix form of the paper with the operator K built above.        */
 /*   t_j = omega1 + omega2 tau_j, omega1 = (tb+ta)/2, omega2 = (tb-ta)/2 */
 /*   y^(0)_j: warm (Kepler) or cold (x0) start                           */
@@ -461,11 +471,28 @@ static int ora_pc_segment_core(const ora_model *m, const ora_opts *o, const doub
   int outcome = ORA_SEG_FAIL_CAP, i;
   for (i = 1; i <= o->max_iters; i++) {
     for (int j = 0; j < n; j++) ora_f(m, o, B ? ephem + (size_t)j * B * 3 : NULL, Y + 6 * j, G + 6 * j);
-    for (int j = 0; j < n; j++) {
-      for (int c = 0; c < 6; c++) {
-        double s = 0.0;
-        for (int k = 0; k < n; k++) s += K[j * n + k] * G[6 * k + c];
-        Ynew[6 * j + c] = x0[c] + w2 * s;
+    if (o->order == 2) {
+      /* second-order form: velocities from the integrated accelerations, then
+         positions from the integrated new velocities (as ora_pc2_segment) */
+      for (int j = 0; j < n; j++)
+        for (int c = 3; c < 6; c++) {
+          double s = 0.0;
+          for (int k = 0; k < n; k++) s += K[j * n + k] * G[6 * k + c];
+          Ynew[6 * j + c] = x0[c] + w2 * s;
+        }
+      for (int j = 0; j < n; j++)
+        for (int c = 0; c < 3; c++) {
+          double s = 0.0;
+          for (int k = 0; k < n; k++) s += K[j * n + k] * Ynew[6 * k + 3 + c];
+          Ynew[6 * j + c] = x0[c] + w2 * s;
+        }
+    } else {
+      for (int j = 0; j < n; j++) {
+        for (int c = 0; c < 6; c++) {
+          double s = 0.0;
+          for (int k = 0; k < n; k++) s += K[j * n + k] * G[6 * k + c];
+          Ynew[6 * j + c] = x0[c] + w2 * s;
+        }
       }
     }
     e = 0.0;
