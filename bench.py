@@ -364,7 +364,7 @@ def run_ours(args, world, rank, local):
     t_plan = time.perf_counter()
     contraction = pc.PC_CONTRACT_SPLIT if args.contraction == "split" else pc.PC_CONTRACT_DMMA
     plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED if mixed else pc.PC_PREC_FP64,
-                                 switch_tol=switch_tol, contraction=contraction)
+                                 switch_tol=switch_tol, contraction=contraction, order=args.order)
     torch.cuda.synchronize(dev)
     plan_ms = 1000.0 * (time.perf_counter() - t_plan)   # operator build + uploads, reported apart
     stream = torch.cuda.Stream(device=dev)
@@ -418,7 +418,7 @@ def run_ours(args, world, rank, local):
         # replay, no instrumentation; then a separate instrumented replay
         plain = None
         if mixed and not args.no_plain:
-            plan64 = pc.plan_from_workload(w, precision=pc.PC_PREC_FP64, contraction=contraction)
+            plan64 = pc.plan_from_workload(w, precision=pc.PC_PREC_FP64, contraction=contraction, order=args.order)
             xf64 = torch.zeros_like(x0)
             st64 = torch.zeros_like(st)
             it64 = torch.zeros_like(it)
@@ -503,6 +503,7 @@ def run_ours(args, world, rank, local):
                        "path": ("mixed FP32->FP64 batched sweep" if mixed else "plain FP64 batched sweep")
                                + " (per-trajectory segments, compaction, DMMA contraction)",
                        "switch_tol": switch_tol if mixed else None,
+                       "sweep_order": args.order,
                        "fp64_contraction": ("exact 8-bit digit products on the bf16 tensor cores"
                                             if args.contraction == "split" else "FP64 tensor cores (DMMA)"),
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}",
@@ -659,6 +660,8 @@ def main(argv=None):
     ap.add_argument("--switch-tol", type=float, default=None,
                     help="FP32 -> FP64 switch threshold (default 1e-6 precision, 0 flyby: when the FP32 change "
                          "stops falling)")
+    ap.add_argument("--order", type=int, choices=[1, 2], default=1,
+                    help="1: the paper's sweep; 2: its second-order form (both arms)")
     ap.add_argument("--contraction", choices=["split", "dmma"], default="split",
                     help="FP64 contraction: exact digit products on the bf16 tensor cores, or the FP64 tensor cores")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")

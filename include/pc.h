@@ -123,12 +123,17 @@ typedef struct {
                           followed by an FP32 solve for the correction to its iterate (up to
                           two per segment attempt) instead of further FP64 sweeps */
   int contraction;     /* PC_CONTRACT_DMMA or PC_CONTRACT_SPLIT: how FP64 sweeps apply the operator */
+  int order;           /* 1: the paper's sweep, y' = x0 + omega2 K f(y); 2: its second-order form
+                          (the paper's Introduction and Conclusion name it as a further gain):
+                          V' = v0 + omega2 K a(R), then R' = r0 + omega2 K V' -- the same fixed point
+                          in about half the sweeps; in FP32 sweeps too; needs PC_CONTRACT_SPLIT
+                          and N <= 255 */
 } pc_options;
 
 /* Fills *o with the defaults: tol 1e-13, relative 1, max_iters 60, max_depth 8,
  * warm_start 1, seg_mode 0, truncated 0, stall_sweeps 5, stall_factor 1e3,
  * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0, refine32 1,
- * contraction PC_CONTRACT_SPLIT.
+ * contraction PC_CONTRACT_SPLIT, order 1.
  * Returns PC_EINVAL if o is NULL. */
 pc_status pc_options_default(pc_options *o);
 

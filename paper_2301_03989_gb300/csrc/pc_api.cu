@@ -100,7 +100,9 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   s.lc[1] = w.lists + 5 * (size_t)w.ld;
   s.lc_cnt = w.ints + 8;
   s.tile_ctr = w.ints + 7;
+  s.tile_ctr2 = w.ints + 12;
   s.fp32_ctr = w.ints + 10;
+  s.order = o.order;
   s.kep_stride = p->kep_stride;
   s.Lint = p->d_Lint;
   s.YK17 = w.YK17;

@@ -99,6 +99,7 @@ constexpr int kKepNodes = 17;  // interpolation nodes of the warm start
 
 struct Sweep {
   int N, n, kpad, rows_pad;  // degree, nodes, padded k extent, padded output rows (nodes 1..N)
+  int order;                 // 1: the paper's sweep; 2: its second-order form
   int kep_stride;            // warm start solved at nodes 0, kep_stride, ..., N (0: at every node)
   const double *Lint;        // [n][17] interpolation weights (kep_stride > 0)
   double *YK17;              // [17][6][ld] Kepler solutions at those nodes
@@ -139,6 +140,7 @@ struct Sweep {
   int *lc_cnt;               // [2]
   int list_cur;
   int *tile_ctr;             // dynamic tile counter of the FP64 contraction
+  int *tile_ctr2;            // the same for the position pass of a second-order sweep
   int *fp32_ctr;             // [2] list-entry counters of the tiled FP32 kernels (new segment, correction),
                              // cleared by the round's set-up kernel
   unsigned long long *cnt64; // [0] FP64, [1] FP32 trajectory-sweeps of this call
@@ -162,7 +164,8 @@ struct Workspace {
   int *lists = nullptr;      // 6 x ld: setup lists [2], FP64 lists [2], correction lists [2]
   int *ints = nullptr;       // [0..1] done counters [finished, stopped], [2..3] setup list counts,
                              // [4] repack count, [5..6] FP64 list counts, [7] tile counter,
-                             // [8..9] correction list counts, [10..11] FP32 list-entry counters
+                             // [8..9] correction list counts, [10..11] FP32 list-entry counters,
+                             // [12] tile counter of the second-order position pass
   int *pos = nullptr;        // [ld] repack destinations
   unsigned long long *cnt64 = nullptr;  // [0] FP64 trajectory-sweeps, [1] FP32 trajectory-sweeps
   unsigned long long *h_cnt64 = nullptr;
@@ -278,10 +281,13 @@ cudaError_t launch_eval_warm(const pc_plan *plan, long long n_pts, const double 
 cudaError_t launch_apply_operator(const pc_plan *plan, long long n_ic, int ld, const double *x0, const double *G,
                                   double *Y, cudaStream_t st);
 // pc_split.cu: the FP64 contraction by exact digit products on the bf16 tensor
-// cores, over the round's FP64 list (diag = 0: Y' = x0 + K G with the change
-// and the residual) or over columns 0..n_ic-1 (diag = 1: Y' only).
-cudaError_t launch_contract_split(const pc_plan *plan, const Sweep &s, const Ctl &c, const double *G,
-                                  const double *Yold, double *Ynew, float *R32, int diag, cudaStream_t st);
+// cores: over the round's FP64 list, Y' = x0 + K G with the change and the
+// residual (SPLIT_FIRST_ORDER), or its second-order form in two passes, the
+// second pass reading omega2 V' from G's velocity rows (SPLIT_SECOND_ORDER);
+// or over columns 0..n_ic-1, Y' only (SPLIT_DIAG).
+enum : int { SPLIT_FIRST_ORDER = 0, SPLIT_DIAG = 1, SPLIT_SECOND_ORDER = 2 };
+cudaError_t launch_contract_split(const pc_plan *plan, const Sweep &s, const Ctl &c, double *G,
+                                  const double *Yold, double *Ynew, float *R32, int mode, cudaStream_t st);
 cudaError_t prepare_split(const pc_plan *plan);
 bool split_supported(const pc_plan *plan);
 }  // namespace pcx

@@ -87,6 +87,7 @@ extern "C" pc_status pc_options_default(pc_options *o) {
   o->max_rounds = 0;
   o->refine32 = 1;
   o->contraction = PC_CONTRACT_SPLIT;
+  o->order = 1;
   return PC_OK;
 }
 
@@ -95,7 +96,8 @@ static pc_status check_options(const pc_options &o) {
       !(o.stall_factor >= 0.0) || !(o.div_limit > 0.0) || (o.seg_mode != 0 && o.seg_mode != 1) ||
       (o.precision != PC_PREC_FP64 && o.precision != PC_PREC_MIXED) || o.max_rounds < 0 ||
       !(o.switch_tol >= 0.0) || (o.refine32 != 0 && o.refine32 != 1) ||
-      (o.contraction != PC_CONTRACT_DMMA && o.contraction != PC_CONTRACT_SPLIT))
+      (o.contraction != PC_CONTRACT_DMMA && o.contraction != PC_CONTRACT_SPLIT) || (o.order != 1 && o.order != 2) ||
+      (o.order == 2 && o.contraction != PC_CONTRACT_SPLIT))
     return PC_EINVAL;
   return PC_OK;
 }
@@ -117,6 +119,7 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
   if (opt) o = *opt;
   if (check_options(o) != PC_OK) return PC_EINVAL;
   if (o.precision == PC_PREC_MIXED && N + 1 > 32 * kMaxNpl) return PC_EINVAL;
+  if (o.order == 2 && N > 255) return PC_EINVAL;  // the second-order sweep runs on the split contraction
 
   pc_plan *p = new (std::nothrow) pc_plan();
   if (!p) return PC_ENOMEM;

@@ -36,14 +36,22 @@ namespace {
 
 constexpr int kSplitThreads = 128;
 constexpr int kSplitTraj = 8;                   // trajectories per column tile
-constexpr int kSplitRows = 6 * kSplitTraj;      // digit rows per slice
 constexpr int kSplitCtasPerSm = 2;
+
+// Epilogues: EPI_FULL the first-order sweep (new iterate, change, residual),
+// EPI_DIAG the kernel-level product, and the two passes of a second-order
+// sweep: EPI_VEL (velocities V' = v0 + K A; also omega2 V' into the velocity
+// rows of G for the next pass) and EPI_POS (positions R' = r0 + K (omega2 V'),
+// then the change and residual of the whole state).
+enum : int { EPI_FULL = 0, EPI_DIAG = 1, EPI_VEL = 2, EPI_POS = 3 };
 
 // k extent of a digit row in shared memory: 16 per k-step plus 8 (304 bytes
 // at 9 k-steps, so the 8 rows of an ldmatrix phase hit distinct banks)
 __host__ __device__ inline int split_ksp(int n_ks) { return 16 * n_ks + 8; }
-__host__ __device__ inline size_t split_smem_bytes(int n_ks) {
-  return sizeof(__nv_bfloat16) * (size_t)kSplitDigits * kSplitRows * split_ksp(n_ks);
+// digit rows per slice: 8 trajectories x nc components, padded to whole 16-row tiles
+__host__ __device__ constexpr int split_mtiles(int nc) { return (8 * nc + 15) / 16; }
+__host__ __device__ inline size_t split_smem_bytes(int n_ks, int nc) {
+  return sizeof(__nv_bfloat16) * (size_t)kSplitDigits * 16 * split_mtiles(nc) * split_ksp(n_ks);
 }
 
 struct SplitOp {
@@ -73,13 +81,20 @@ __device__ __forceinline__ double pow2i(int e) {
   return ldexp(1.0, e);
 }
 
-template <bool DIAG>
+// NC components (6: the first-order sweep; 3: one pass of the second-order
+// sweep) starting at component Q0 of G.  Digit row q*8 + tt holds component
+// Q0 + q of the tile's trajectory tt.
+template <int NC, int Q0, int EPI>
 __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
-    k_contract_split(Sweep s, Ctl c, SplitOp op, const double *__restrict__ G, const double *__restrict__ Yold,
+    k_contract_split(Sweep s, Ctl c, SplitOp op, double *__restrict__ G, const double *__restrict__ Yold,
                      double *__restrict__ Ynew, float *__restrict__ R32) {
+  constexpr bool DIAG = EPI == EPI_DIAG;
+  constexpr int kRows = 8 * NC;                    // digit rows in use
+  constexpr int MT = split_mtiles(NC);             // 16-row tiles (3 or 2)
+  constexpr int kRowsPad = 16 * MT;
   extern __shared__ __align__(16) unsigned char split_sm[];
-  __nv_bfloat16 *Gd = reinterpret_cast<__nv_bfloat16 *>(split_sm);  // [7][48][ksp]
-  __shared__ int colB[kSplitRows];       // largest biased exponent of each column
+  __nv_bfloat16 *Gd = reinterpret_cast<__nv_bfloat16 *>(split_sm);  // [7][16 MT][ksp]
+  __shared__ int colB[kRows];            // largest biased exponent of each column
   __shared__ int colm[kSplitTraj];       // the tile's trajectories (slots), -1 past the end
   __shared__ int bad[kSplitTraj];        // an inf or NaN in one of the trajectory's columns
   __shared__ unsigned long long emax_sh[kSplitTraj];
@@ -90,17 +105,23 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
   const int ncols = DIAG ? (int)s.n_ic : s.l64_cnt[s.list_cur];
   const int *map = DIAG ? nullptr : s.l64[s.list_cur];
   const int n_tiles = (ncols + kSplitTraj - 1) / kSplitTraj;
-  if (tid < kSplitRows) colB[tid] = 0;
+  if (tid < kRows) colB[tid] = 0;
   if (tid < kSplitTraj) {
     bad[tid] = 0;
     emax_sh[tid] = 0ULL;
   }
+  // the padding rows of the last 16-row tile stay zero
+  if (kRowsPad > kRows)
+    for (int i = tid; i < kSplitDigits * (kRowsPad - kRows) * ksp; i += kSplitThreads) {
+      const int a = i / ((kRowsPad - kRows) * ksp), r = i % ((kRowsPad - kRows) * ksp);
+      Gd[((size_t)a * kRowsPad + kRows) * ksp + r] = __int2bfloat16_rn(0);
+    }
   for (int iter = 0;; iter++) {
     int tile;
     if (DIAG) {
       tile = blockIdx.x + iter * gridDim.x;
     } else {
-      if (tid == 0) tile_sh = atomicAdd(s.tile_ctr, 1);
+      if (tid == 0) tile_sh = atomicAdd(EPI == EPI_POS ? s.tile_ctr2 : s.tile_ctr, 1);
       __syncthreads();
       tile = tile_sh;
     }
@@ -109,31 +130,32 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
     if (tid < kSplitTraj) colm[tid] = (e0 + tid < ncols) ? (DIAG ? e0 + tid : map[e0 + tid]) : -1;
     __syncthreads();
     // ---- column exponents (shared-memory max over the nodes)
-    for (int i = tid; i < kSplitRows * n; i += kSplitThreads) {
-      const int col = i % kSplitRows, k = i / kSplitRows;
+    for (int i = tid; i < kRows * n; i += kSplitThreads) {
+      const int col = i % kRows, k = i / kRows;
       const int m = colm[col & 7];
       if (m >= 0) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(G[((size_t)k * 6 + (col >> 3)) * ld + m]);
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(G[((size_t)k * 6 + Q0 + (col >> 3)) * ld + m]);
         atomicMax(&colB[col], (int)((b >> 52) & 0x7ff));
       }
     }
     // node 0 of the new iterate is the segment's initial state
-    if (tid < kSplitRows) {
-      const int q = tid >> 3, m = colm[tid & 7];
+    if (tid < kRows) {
+      const int q = Q0 + (tid >> 3), m = colm[tid & 7];
       if (m >= 0) Ynew[(size_t)q * ld + m] = c.x[(size_t)q * ld + m];
     }
     __syncthreads();
     // ---- digits, two nodes per thread and step (bf16 pairs along k)
-    for (int i = tid; i < kSplitRows * (kext / 2); i += kSplitThreads) {
+    for (int i = tid; i < kRows * (kext / 2); i += kSplitThreads) {
       const int k = 2 * (i % (kext / 2)), col = i / (kext / 2);
-      const int m = colm[col & 7], q = col >> 3, Bc = colB[col];
+      const int m = colm[col & 7], q = Q0 + (col >> 3), Bc = colB[col];
       if (Bc == 0x7ff && (i % (kext / 2)) == 0) bad[col & 7] = 1;
       int d0[kSplitDigits], d1[kSplitDigits];
       split_digits7((m >= 0 && k < n) ? G[((size_t)k * 6 + q) * ld + m] : 0.0, Bc, d0);
       split_digits7((m >= 0 && k + 1 < n) ? G[((size_t)(k + 1) * 6 + q) * ld + m] : 0.0, Bc, d1);
 #pragma unroll
       for (int a = 0; a < kSplitDigits; a++)
-        *reinterpret_cast<__nv_bfloat162 *>(Gd + ((size_t)a * kSplitRows + col) * ksp + k) =
+        *reinterpret_cast<__nv_bfloat162 *>(Gd + ((size_t)a * kRowsPad + col) * ksp + k) =
             __halves2bfloat162(__int2bfloat16_rn(d0[a]), __int2bfloat16_rn(d1[a]));
     }
     __syncthreads();
@@ -141,9 +163,9 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
     const int g = lane >> 2, t = lane & 3;
     const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
     for (int nt = w; nt < op.n_nt; nt += kSplitThreads / 32) {
-      float acc[3][kSplitDigits][4];
+      float acc[MT][kSplitDigits][4];
 #pragma unroll
-      for (int mt = 0; mt < 3; mt++)
+      for (int mt = 0; mt < MT; mt++)
 #pragma unroll
         for (int dd = 0; dd < kSplitDigits; dd++)
 #pragma unroll
@@ -155,14 +177,14 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
         for (int b = 0; b < kSplitDigits; b++) bf[b] = __ldg(kf + ((size_t)ks * kSplitDigits + b) * 32);
 #pragma unroll
         for (int a = 0; a < kSplitDigits; a++) {
-          unsigned af[3][4];
+          unsigned af[MT][4];
 #pragma unroll
-          for (int mt = 0; mt < 3; mt++)
-            ldsm_x4(af[mt], Gd + ((size_t)a * kSplitRows + mt * 16 + arow) * ksp + ks * 16 + acol);
+          for (int mt = 0; mt < MT; mt++)
+            ldsm_x4(af[mt], Gd + ((size_t)a * kRowsPad + mt * 16 + arow) * ksp + ks * 16 + acol);
 #pragma unroll
           for (int b = 0; b < kSplitDigits - a; b++)
 #pragma unroll
-            for (int mt = 0; mt < 3; mt++) mma_bf16_16816(acc[mt][a + b], af[mt], bf[b]);
+            for (int mt = 0; mt < MT; mt++) mma_bf16_16816(acc[mt][a + b], af[mt], bf[b]);
         }
       }
       // ---- epilogue: trajectory g of the tile at nodes 1 + nt*8 + 2t + {0, 1}
@@ -173,9 +195,10 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
         const int r = nt * 8 + 2 * t + e, j = r + 1;
         if (m < 0 || j > N) continue;
         const int kx = op.kexp[r];
-        double yn[6];
+        const size_t base = (size_t)j * 6 * ld + m;
+        double yq[NC];
 #pragma unroll
-        for (int q = 0; q < 6; q++) {
+        for (int q = 0; q < NC; q++) {
           const int mt = q >> 1, idx = (q & 1) * 2 + e;
           long long S[kSplitDigits];
 #pragma unroll
@@ -183,15 +206,23 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
           const long long vhi = S[0] * (1LL << 24) + S[1] * (1LL << 16) + S[2] * (1LL << 8) + S[3];
           const long long vlo = S[4] * (1LL << 16) + S[5] * (1LL << 8) + S[6];
           const double v = fma((double)vlo, 0x1p-24, (double)vhi) * pow2i(kx + colB[q * 8 + g] - 2042 - 40);
-          yn[q] = c.x[(size_t)q * ld + m] + v;
+          yq[q] = c.x[(size_t)(Q0 + q) * ld + m] + v;
         }
         if (bad[g])
 #pragma unroll
-          for (int q = 0; q < 6; q++) yn[q] = __longlong_as_double(0x7FF8000000000000LL);
-        const size_t base = (size_t)j * 6 * ld + m;
+          for (int q = 0; q < NC; q++) yq[q] = __longlong_as_double(0x7FF8000000000000LL);
 #pragma unroll
-        for (int q = 0; q < 6; q++) Ynew[base + (size_t)q * ld] = yn[q];
-        if (!DIAG) {
+        for (int q = 0; q < NC; q++) Ynew[base + (size_t)(Q0 + q) * ld] = yq[q];
+        if (EPI == EPI_VEL) {
+          // omega2 V' is what the position pass integrates
+          const double w2 = c.w2[m];
+#pragma unroll
+          for (int q = 0; q < 3; q++) G[base + (size_t)q * ld] = w2 * yq[q];
+        }
+        if (EPI == EPI_FULL || EPI == EPI_POS) {
+          double yn[6];
+#pragma unroll
+          for (int q = 0; q < 6; q++) yn[q] = (q < NC) ? yq[q] : Ynew[base + (size_t)q * ld];
           double d[6];
 #pragma unroll
           for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
@@ -211,7 +242,7 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
           e2 = nanmax(e2, nanmax(dr, dv));
         }
       }
-      if (!DIAG) {
+      if (EPI == EPI_FULL || EPI == EPI_POS) {
         e2 = nanmax(e2, __shfl_xor_sync(0xffffffffu, e2, 1));
         e2 = nanmax(e2, __shfl_xor_sync(0xffffffffu, e2, 2));
         if (t == 0 && m >= 0) atomicMax(&emax_sh[g], err_bits(e2));
@@ -221,13 +252,31 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
     // the tile holds every node of its trajectories: the maximum is final
     if (tid < kSplitTraj) {
       const int m = colm[tid];
-      if (!DIAG && m >= 0) c.err[m] = err_bits(sqrt(__longlong_as_double((long long)emax_sh[tid])));
+      if ((EPI == EPI_FULL || EPI == EPI_POS) && m >= 0)
+        c.err[m] = err_bits(sqrt(__longlong_as_double((long long)emax_sh[tid])));
       bad[tid] = 0;
       emax_sh[tid] = 0ULL;
     }
-    if (tid < kSplitRows) colB[tid] = 0;
+    if (tid < kRows) colB[tid] = 0;
     __syncthreads();  // shared memory is reused by the next tile
   }
+}
+
+template <int NC, int Q0, int EPI>
+cudaError_t split_attr(const pc_plan *p) {
+  return cudaFuncSetAttribute(k_contract_split<NC, Q0, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)split_smem_bytes(p->split_ks, NC));
+}
+
+template <int NC, int Q0, int EPI>
+void split_launch(const pc_plan *p, const Sweep &s, const Ctl &c, double *G, const double *Yold, double *Ynew,
+                  float *R32, long long cols, cudaStream_t st) {
+  SplitOp op{reinterpret_cast<const uint2 *>(p->d_Kdig), p->d_Kexp, p->split_nt, p->split_ks};
+  const long long tiles = (cols + kSplitTraj - 1) / kSplitTraj;
+  const int sms = p->num_sms > 0 ? p->num_sms : 152;
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((long long)sms * kSplitCtasPerSm, tiles));
+  k_contract_split<NC, Q0, EPI><<<blocks, kSplitThreads, split_smem_bytes(p->split_ks, NC), st>>>(s, c, op, G, Yold,
+                                                                                                 Ynew, R32);
 }
 
 }  // namespace
@@ -236,25 +285,24 @@ bool split_supported(const pc_plan *p) { return p->d_Kdig != nullptr; }
 
 cudaError_t prepare_split(const pc_plan *p) {
   if (!split_supported(p)) return cudaSuccess;
-  const int bytes = (int)split_smem_bytes(p->split_ks);
-  cudaError_t e = cudaFuncSetAttribute(k_contract_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_contract_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = split_attr<6, 0, EPI_FULL>(p);
+  if (e == cudaSuccess) e = split_attr<6, 0, EPI_DIAG>(p);
+  if (e == cudaSuccess) e = split_attr<3, 3, EPI_VEL>(p);
+  if (e == cudaSuccess) e = split_attr<3, 0, EPI_POS>(p);
   return e;
 }
 
-cudaError_t launch_contract_split(const pc_plan *p, const Sweep &s, const Ctl &c, const double *G, const double *Yold,
-                                  double *Ynew, float *R32, int diag, cudaStream_t st) {
-  SplitOp op{reinterpret_cast<const uint2 *>(p->d_Kdig), p->d_Kexp, p->split_nt, p->split_ks};
-  const long long cols = diag ? s.n_ic : s.A;
-  const long long tiles = (cols + kSplitTraj - 1) / kSplitTraj;
-  const int sms = p->num_sms > 0 ? p->num_sms : 152;
-  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((long long)sms * kSplitCtasPerSm, tiles));
-  const size_t smem = split_smem_bytes(p->split_ks);
-  if (diag)
-    k_contract_split<true><<<blocks, kSplitThreads, smem, st>>>(s, c, op, G, nullptr, Ynew, nullptr);
-  else
-    k_contract_split<false><<<blocks, kSplitThreads, smem, st>>>(s, c, op, G, Yold, Ynew, R32);
+cudaError_t launch_contract_split(const pc_plan *p, const Sweep &s, const Ctl &c, double *G, const double *Yold,
+                                  double *Ynew, float *R32, int mode, cudaStream_t st) {
+  switch (mode) {
+    case SPLIT_DIAG: split_launch<6, 0, EPI_DIAG>(p, s, c, G, nullptr, Ynew, nullptr, s.n_ic, st); break;
+    case SPLIT_SECOND_ORDER:
+      // velocities first; the position pass reads omega2 V' from G's velocity rows
+      split_launch<3, 3, EPI_VEL>(p, s, c, G, nullptr, Ynew, nullptr, s.A, st);
+      split_launch<3, 0, EPI_POS>(p, s, c, G, Yold, Ynew, R32, s.A, st);
+      break;
+    default: split_launch<6, 0, EPI_FULL>(p, s, c, G, Yold, Ynew, R32, s.A, st); break;
+  }
   return cudaGetLastError();
 }
 

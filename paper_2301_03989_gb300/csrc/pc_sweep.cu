@@ -790,7 +790,40 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
       // this node's row of the contraction
 #pragma unroll
       for (int q = 0; q < 6; q++) acc[q] = 0.0f;
-      if (node) {
+      if (s.order == 2) {
+        // second-order form: velocity rows from the accelerations, then the
+        // position rows from omega2 times the new velocity deviations
+        if (node) {
+          const float *kr = K32T + j;
+#pragma unroll 8
+          for (int k = 0; k < n; k++) {
+            const float kv = __ldg(kr + (size_t)k * np);
+            const float *g = Gs + k * 6;
+            acc[3] = fmaf(kv, g[3], acc[3]);
+            acc[4] = fmaf(kv, g[4], acc[4]);
+            acc[5] = fmaf(kv, g[5], acc[5]);
+          }
+        }
+        __syncthreads();  // every thread has read the acceleration rows
+        // the position rows integrate the change of the sweep's velocities:
+        // delta_v (new segment) or c_v - R_v (correction after a second-order
+        // FP64 sweep, whose residual already holds R_v)
+        if (node)
+#pragma unroll
+          for (int q = 0; q < 3; q++) Gs[j * 6 + q] = w2f * acc[3 + q];
+        __syncthreads();
+        if (node) {
+          const float *kr = K32T + j;
+#pragma unroll 8
+          for (int k = 0; k < n; k++) {
+            const float kv = __ldg(kr + (size_t)k * np);
+            const float *g = Gs + k * 6;
+            acc[0] = fmaf(kv, g[0], acc[0]);
+            acc[1] = fmaf(kv, g[1], acc[1]);
+            acc[2] = fmaf(kv, g[2], acc[2]);
+          }
+        }
+      } else if (node) {
         const float *kr = K32T + j;
 #pragma unroll 8
         for (int k = 0; k < n; k++) {
@@ -1138,13 +1171,11 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       }
     }
     __syncthreads();
-    // the thread's R x 6 block of K G, k ascending
+    // the thread's R x 6 block of K G, k ascending (second-order form: the
+    // velocity rows from the accelerations, then the position rows from
+    // omega2 times the new velocity deviations written into the table)
     float emax = 0.0f, dmax = 0.0f;
-    if (live) {
-#pragma unroll
-      for (int i = 0; i < R; i++)
-#pragma unroll
-        for (int q = 0; q < 6; q++) acc[i][q] = 0.0f;
+    auto contract = [&](int q0, int nq) {
 #pragma unroll 2
       for (int k = 0; k < n; k++) {
         float kv[R];
@@ -1157,18 +1188,55 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
           kv[i + 2] = k4.z;
           kv[i + 3] = k4.w;
         }
-        const float2 *g2 = reinterpret_cast<const float2 *>(Gk + (size_t)k * 6 * T);
-        const float2 ga = g2[0], gb = g2[1], gc = g2[2];
+        const float *gk = Gk + (size_t)k * 6 * T;
+        if (nq == 6) {
+          const float2 *g2 = reinterpret_cast<const float2 *>(gk);
+          const float2 ga = g2[0], gb = g2[1], gc = g2[2];
 #pragma unroll
-        for (int i = 0; i < R; i++) {
-          acc[i][0] = fmaf(kv[i], ga.x, acc[i][0]);
-          acc[i][1] = fmaf(kv[i], ga.y, acc[i][1]);
-          acc[i][2] = fmaf(kv[i], gb.x, acc[i][2]);
-          acc[i][3] = fmaf(kv[i], gb.y, acc[i][3]);
-          acc[i][4] = fmaf(kv[i], gc.x, acc[i][4]);
-          acc[i][5] = fmaf(kv[i], gc.y, acc[i][5]);
+          for (int i = 0; i < R; i++) {
+            acc[i][0] = fmaf(kv[i], ga.x, acc[i][0]);
+            acc[i][1] = fmaf(kv[i], ga.y, acc[i][1]);
+            acc[i][2] = fmaf(kv[i], gb.x, acc[i][2]);
+            acc[i][3] = fmaf(kv[i], gb.y, acc[i][3]);
+            acc[i][4] = fmaf(kv[i], gc.x, acc[i][4]);
+            acc[i][5] = fmaf(kv[i], gc.y, acc[i][5]);
+          }
+        } else {
+          const float g0 = gk[q0], g1 = gk[q0 + 1], g2v = gk[q0 + 2];
+#pragma unroll
+          for (int i = 0; i < R; i++) {
+            acc[i][q0] = fmaf(kv[i], g0, acc[i][q0]);
+            acc[i][q0 + 1] = fmaf(kv[i], g1, acc[i][q0 + 1]);
+            acc[i][q0 + 2] = fmaf(kv[i], g2v, acc[i][q0 + 2]);
+          }
         }
       }
+    };
+    if (live)
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int q = 0; q < 6; q++) acc[i][q] = 0.0f;
+    if (s.order == 2) {
+      if (live) {
+        contract(3, 3);
+#pragma unroll
+        for (int i = 0; i < R; i++) {
+          const int j = j0 + i;
+          // the position rows integrate the change of the sweep's velocities:
+          // delta_v (new segment) or c_v - R_v (correction after a
+          // second-order FP64 sweep, whose residual already holds R_v)
+          if (j <= N)
+#pragma unroll
+            for (int q = 0; q < 3; q++) Gs[((size_t)j * T + t) * 6 + q] = w2f * acc[i][3 + q];
+        }
+      }
+      __syncthreads();  // the table's velocity rows hold the new deviations
+      if (live) contract(0, 3);
+    } else if (live) {
+      contract(0, 6);
+    }
+    if (live) {
       // change and size of the deviation, relative to the iterate
 #pragma unroll
       for (int i = 0; i < R; i++) {
@@ -1367,7 +1435,10 @@ __global__ void k_control(Sweep s, Ctl c, const double *__restrict__ tails, cons
   const int list_next = s.list_cur ^ 1;
   int out = SEG_CONTINUE;
   double e_sweep = 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *s.tile_ctr = 0;  // this round's contraction is over
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // this round's contraction is over
+    *s.tile_ctr = 0;
+    *s.tile_ctr2 = 0;
+  }
   if (ready) {
     c.need_setup[m] = 0;
     c.phase[m] = PH_ITER;
@@ -1770,7 +1841,7 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   if (ev) cudaEventRecord(ev[3], st);
   if (use_split(p)) {
     // exact digit products on the bf16 tensor cores
-    e = launch_contract_split(p, s, c, w.G, Yc, Yn, R32, 0, st);
+    e = launch_contract_split(p, s, c, w.G, Yc, Yn, R32, s.order == 2 ? SPLIT_SECOND_ORDER : SPLIT_FIRST_ORDER, st);
     if (e != cudaSuccess) return e;
   } else {
     // persistent FP64 contraction: contract_ctas_per_sm CTAs of kSplit warps per SM
@@ -1854,7 +1925,7 @@ cudaError_t launch_apply_operator(const pc_plan *p, long long n_ic, int ld, cons
   if (use_split(p)) {
     const cudaError_t e = prepare_split(p);
     if (e != cudaSuccess) return e;
-    return launch_contract_split(p, s, c, G, nullptr, Y, nullptr, 1, st);
+    return launch_contract_split(p, s, c, const_cast<double *>(G), nullptr, Y, nullptr, SPLIT_DIAG, st);
   }
   const long long tiles = (long long)(s.rows_pad / 16) * ((n_ic + 7) / 8);
   k_contract_diag<<<(unsigned)std::min<long long>(tiles, sm_ctas(p, 8)), 32 * kSplit, 0, st>>>(s, c, p->d_K, G, Y);

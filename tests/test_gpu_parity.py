@@ -129,11 +129,12 @@ def pmap(fn, items):
         return list(ex.map(fn, items))
 
 
-def _segment_local(ora, w, g, idx, tf=None):
+def _segment_local(ora, w, g, idx, tf=None, order=1):
     """Oracle restarted at the GPU's checkpoints; returns max relative error at
     the next checkpoint (or the end state)."""
     m = ora.Model.from_workload(w)
-    o = ora.Opts(N=w.N, segments=1, seg_mode=0, tol=w.tol, max_iters=w.max_iters, max_depth=0, trunc_tol=0.0)
+    o = ora.Opts(N=w.N, segments=1, seg_mode=0, tol=w.tol, max_iters=w.max_iters, max_depth=0, trunc_tol=0.0,
+                 order=order)
     tf = w.tf if tf is None else tf
     jobs = []
     for i in idx:
