@@ -15,15 +15,16 @@
 // the two exponents.  The pairs with a + b > 8 are below 2^-64 of the scale
 // and dropped; the result's error is below that of an FP64 dot product.
 //
-// One CTA (4 warps) takes a column tile of 8 trajectories x 6 components from
-// a counter: it writes the tile's digits to shared memory as 7 x 48 rows of
-// bf16 (row q*8 + tt: component q of trajectory tt), then each warp runs
+// One CTA (4 warps) takes a column tile of 8 trajectories x 6 components (16 x
+// 3 in a pass of the second-order sweep) from a counter: it writes the tile's
+// digits to shared memory as 7 x 48 rows of bf16 (row q*8 + tt: component q
+// of trajectory tt), then each warp runs
 // node tiles of 8 output nodes: C[(q, tt)][node] = sum_k G~[k][(q, tt)]
 // K~[node][k] with the force digits as the A operand (ldmatrix from shared
 // memory) and the operator digits as the B operand (fragments precomputed by
-// the plan, 128-bit loads from L2).  A thread's accumulators then hold all six
-// components of one trajectory at two nodes, which is what the epilogue
-// (new iterate, change, residual) needs.
+// the plan, 64-bit loads from L2).  A thread's accumulators then hold every
+// component of its trajectories at two nodes, which is what the epilogue (new
+// iterate, change, residual) needs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -35,7 +36,6 @@ namespace pcx {
 namespace {
 
 constexpr int kSplitThreads = 128;
-constexpr int kSplitTraj = 8;                   // trajectories per column tile
 constexpr int kSplitCtasPerSm = 2;
 
 // Epilogues: EPI_FULL the first-order sweep (new iterate, change, residual),
@@ -48,10 +48,12 @@ enum : int { EPI_FULL = 0, EPI_DIAG = 1, EPI_VEL = 2, EPI_POS = 3 };
 // k extent of a digit row in shared memory: 16 per k-step plus 8 (304 bytes
 // at 9 k-steps, so the 8 rows of an ldmatrix phase hit distinct banks)
 __host__ __device__ inline int split_ksp(int n_ks) { return 16 * n_ks + 8; }
-// digit rows per slice: 8 trajectories x nc components, padded to whole 16-row tiles
-__host__ __device__ constexpr int split_mtiles(int nc) { return (8 * nc + 15) / 16; }
-__host__ __device__ inline size_t split_smem_bytes(int n_ks, int nc) {
-  return sizeof(__nv_bfloat16) * (size_t)kSplitDigits * 16 * split_mtiles(nc) * split_ksp(n_ks);
+// digit rows per slice: 48 = 3 tiles of 16 rows, 8 trajectories x 6 components
+// or 16 trajectories x 3 components
+constexpr int kSplitRows = 48;
+__host__ __device__ constexpr int split_traj(int nc) { return kSplitRows / nc; }
+__host__ __device__ inline size_t split_smem_bytes(int n_ks) {
+  return sizeof(__nv_bfloat16) * (size_t)kSplitDigits * kSplitRows * split_ksp(n_ks);
 }
 
 struct SplitOp {
@@ -82,40 +84,36 @@ __device__ __forceinline__ double pow2i(int e) {
 }
 
 // NC components (6: the first-order sweep; 3: one pass of the second-order
-// sweep) starting at component Q0 of G.  Digit row q*8 + tt holds component
-// Q0 + q of the tile's trajectory tt.
+// sweep) starting at component Q0 of G, for TRAJ = 48 / NC trajectories per
+// tile.  Digit row q*TRAJ + tt holds component Q0 + q of the tile's
+// trajectory tt; a thread's accumulators hold all NC components of
+// trajectories g + 8h (h < TRAJ / 8) at two nodes.
 template <int NC, int Q0, int EPI>
 __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
     k_contract_split(Sweep s, Ctl c, SplitOp op, double *__restrict__ G, const double *__restrict__ Yold,
                      double *__restrict__ Ynew, float *__restrict__ R32) {
   constexpr bool DIAG = EPI == EPI_DIAG;
-  constexpr int kRows = 8 * NC;                    // digit rows in use
-  constexpr int MT = split_mtiles(NC);             // 16-row tiles (3 or 2)
-  constexpr int kRowsPad = 16 * MT;
+  constexpr int TRAJ = split_traj(NC);             // trajectories per tile
+  constexpr int TPT = TRAJ / 8;                    // of them per thread
+  constexpr int kRows = kSplitRows, MT = 3, kRowsPad = kSplitRows;
   extern __shared__ __align__(16) unsigned char split_sm[];
-  __nv_bfloat16 *Gd = reinterpret_cast<__nv_bfloat16 *>(split_sm);  // [7][16 MT][ksp]
+  __nv_bfloat16 *Gd = reinterpret_cast<__nv_bfloat16 *>(split_sm);  // [7][48][ksp]
   __shared__ int colB[kRows];            // largest biased exponent of each column
-  __shared__ int colm[kSplitTraj];       // the tile's trajectories (slots), -1 past the end
-  __shared__ int bad[kSplitTraj];        // an inf or NaN in one of the trajectory's columns
-  __shared__ unsigned long long emax_sh[kSplitTraj];
+  __shared__ int colm[TRAJ];             // the tile's trajectories (slots), -1 past the end
+  __shared__ int bad[TRAJ];              // an inf or NaN in one of the trajectory's columns
+  __shared__ unsigned long long emax_sh[TRAJ];
   __shared__ int tile_sh;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int N = s.N, n = s.n, ld = s.ld;
   const int ksp = split_ksp(op.n_ks), kext = 16 * op.n_ks;
   const int ncols = DIAG ? (int)s.n_ic : s.l64_cnt[s.list_cur];
   const int *map = DIAG ? nullptr : s.l64[s.list_cur];
-  const int n_tiles = (ncols + kSplitTraj - 1) / kSplitTraj;
+  const int n_tiles = (ncols + TRAJ - 1) / TRAJ;
   if (tid < kRows) colB[tid] = 0;
-  if (tid < kSplitTraj) {
+  if (tid < TRAJ) {
     bad[tid] = 0;
     emax_sh[tid] = 0ULL;
   }
-  // the padding rows of the last 16-row tile stay zero
-  if (kRowsPad > kRows)
-    for (int i = tid; i < kSplitDigits * (kRowsPad - kRows) * ksp; i += kSplitThreads) {
-      const int a = i / ((kRowsPad - kRows) * ksp), r = i % ((kRowsPad - kRows) * ksp);
-      Gd[((size_t)a * kRowsPad + kRows) * ksp + r] = __int2bfloat16_rn(0);
-    }
   for (int iter = 0;; iter++) {
     int tile;
     if (DIAG) {
@@ -126,30 +124,30 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
       tile = tile_sh;
     }
     if (tile >= n_tiles) break;
-    const int e0 = tile * kSplitTraj;
-    if (tid < kSplitTraj) colm[tid] = (e0 + tid < ncols) ? (DIAG ? e0 + tid : map[e0 + tid]) : -1;
+    const int e0 = tile * TRAJ;
+    if (tid < TRAJ) colm[tid] = (e0 + tid < ncols) ? (DIAG ? e0 + tid : map[e0 + tid]) : -1;
     __syncthreads();
     // ---- column exponents (shared-memory max over the nodes)
     for (int i = tid; i < kRows * n; i += kSplitThreads) {
       const int col = i % kRows, k = i / kRows;
-      const int m = colm[col & 7];
+      const int m = colm[col % TRAJ];
       if (m >= 0) {
         const unsigned long long b =
-            (unsigned long long)__double_as_longlong(G[((size_t)k * 6 + Q0 + (col >> 3)) * ld + m]);
+            (unsigned long long)__double_as_longlong(G[((size_t)k * 6 + Q0 + col / TRAJ) * ld + m]);
         atomicMax(&colB[col], (int)((b >> 52) & 0x7ff));
       }
     }
     // node 0 of the new iterate is the segment's initial state
     if (tid < kRows) {
-      const int q = Q0 + (tid >> 3), m = colm[tid & 7];
+      const int q = Q0 + tid / TRAJ, m = colm[tid % TRAJ];
       if (m >= 0) Ynew[(size_t)q * ld + m] = c.x[(size_t)q * ld + m];
     }
     __syncthreads();
     // ---- digits, two nodes per thread and step (bf16 pairs along k)
     for (int i = tid; i < kRows * (kext / 2); i += kSplitThreads) {
       const int k = 2 * (i % (kext / 2)), col = i / (kext / 2);
-      const int m = colm[col & 7], q = Q0 + (col >> 3), Bc = colB[col];
-      if (Bc == 0x7ff && (i % (kext / 2)) == 0) bad[col & 7] = 1;
+      const int m = colm[col % TRAJ], q = Q0 + col / TRAJ, Bc = colB[col];
+      if (Bc == 0x7ff && (i % (kext / 2)) == 0) bad[col % TRAJ] = 1;
       int d0[kSplitDigits], d1[kSplitDigits];
       split_digits7((m >= 0 && k < n) ? G[((size_t)k * 6 + q) * ld + m] : 0.0, Bc, d0);
       split_digits7((m >= 0 && k + 1 < n) ? G[((size_t)(k + 1) * 6 + q) * ld + m] : 0.0, Bc, d1);
@@ -187,70 +185,74 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
             for (int mt = 0; mt < MT; mt++) mma_bf16_16816(acc[mt][a + b], af[mt], bf[b]);
         }
       }
-      // ---- epilogue: trajectory g of the tile at nodes 1 + nt*8 + 2t + {0, 1}
-      const int m = colm[g];
-      double e2 = 0.0;
+      // ---- epilogue: trajectories g + 8h of the tile at nodes 1 + nt*8 + 2t + {0, 1}
 #pragma unroll
-      for (int e = 0; e < 2; e++) {
-        const int r = nt * 8 + 2 * t + e, j = r + 1;
-        if (m < 0 || j > N) continue;
-        const int kx = op.kexp[r];
-        const size_t base = (size_t)j * 6 * ld + m;
-        double yq[NC];
+      for (int h = 0; h < TPT; h++) {
+        const int tt = g + 8 * h, m = colm[tt];
+        double e2 = 0.0;
 #pragma unroll
-        for (int q = 0; q < NC; q++) {
-          const int mt = q >> 1, idx = (q & 1) * 2 + e;
-          long long S[kSplitDigits];
+        for (int e = 0; e < 2; e++) {
+          const int r = nt * 8 + 2 * t + e, j = r + 1;
+          if (m < 0 || j > N) continue;
+          const int kx = op.kexp[r];
+          const size_t base = (size_t)j * 6 * ld + m;
+          double yq[NC];
 #pragma unroll
-          for (int dd = 0; dd < kSplitDigits; dd++) S[dd] = (long long)__float2int_rn(acc[mt][dd][idx]);
-          const long long vhi = S[0] * (1LL << 24) + S[1] * (1LL << 16) + S[2] * (1LL << 8) + S[3];
-          const long long vlo = S[4] * (1LL << 16) + S[5] * (1LL << 8) + S[6];
-          const double v = fma((double)vlo, 0x1p-24, (double)vhi) * pow2i(kx + colB[q * 8 + g] - 2042 - 40);
-          yq[q] = c.x[(size_t)(Q0 + q) * ld + m] + v;
-        }
-        if (bad[g])
+          for (int q = 0; q < NC; q++) {
+            const int row = q * TRAJ + tt;  // digit row; g < 8, so its tile and half are compile-time
+            const int mt = (q * TRAJ + 8 * h) >> 4, idx = (((q * TRAJ + 8 * h) >> 3) & 1) * 2 + e;
+            long long S[kSplitDigits];
 #pragma unroll
-          for (int q = 0; q < NC; q++) yq[q] = __longlong_as_double(0x7FF8000000000000LL);
+            for (int dd = 0; dd < kSplitDigits; dd++) S[dd] = (long long)__float2int_rn(acc[mt][dd][idx]);
+            const long long vhi = S[0] * (1LL << 24) + S[1] * (1LL << 16) + S[2] * (1LL << 8) + S[3];
+            const long long vlo = S[4] * (1LL << 16) + S[5] * (1LL << 8) + S[6];
+            const double v = fma((double)vlo, 0x1p-24, (double)vhi) * pow2i(kx + colB[row] - 2042 - 40);
+            yq[q] = c.x[(size_t)(Q0 + q) * ld + m] + v;
+          }
+          if (bad[tt])
 #pragma unroll
-        for (int q = 0; q < NC; q++) Ynew[base + (size_t)(Q0 + q) * ld] = yq[q];
-        if (EPI == EPI_VEL) {
-          // omega2 V' is what the position pass integrates
-          const double w2 = c.w2[m];
+            for (int q = 0; q < NC; q++) yq[q] = __longlong_as_double(0x7FF8000000000000LL);
 #pragma unroll
-          for (int q = 0; q < 3; q++) G[base + (size_t)q * ld] = w2 * yq[q];
+          for (int q = 0; q < NC; q++) Ynew[base + (size_t)(Q0 + q) * ld] = yq[q];
+          if (EPI == EPI_VEL) {
+            // omega2 V' is what the position pass integrates
+            const double w2 = c.w2[m];
+#pragma unroll
+            for (int q = 0; q < 3; q++) G[base + (size_t)q * ld] = w2 * yq[q];
+          }
+          if (EPI == EPI_FULL || EPI == EPI_POS) {
+            double yn[6];
+#pragma unroll
+            for (int q = 0; q < 6; q++) yn[q] = (q < NC) ? yq[q] : Ynew[base + (size_t)q * ld];
+            double d[6];
+#pragma unroll
+            for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
+            if (R32)  // the sweep's residual, for an FP32 correction solve next round
+#pragma unroll
+              for (int q = 0; q < 6; q++) R32[base + (size_t)q * ld] = (float)d[q];
+            // squared change of |r| and |v| relative to the new iterate (one
+            // square root per trajectory, after the maximum)
+            double dr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double dv = d[3] * d[3] + d[4] * d[4] + d[5] * d[5];
+            if (s.relative) {
+              const double nr = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
+              const double nv = yn[3] * yn[3] + yn[4] * yn[4] + yn[5] * yn[5];
+              if (nr > 0.0) dr = dr / nr;
+              if (nv > 0.0) dv = dv / nv;
+            }
+            e2 = nanmax(e2, nanmax(dr, dv));
+          }
         }
         if (EPI == EPI_FULL || EPI == EPI_POS) {
-          double yn[6];
-#pragma unroll
-          for (int q = 0; q < 6; q++) yn[q] = (q < NC) ? yq[q] : Ynew[base + (size_t)q * ld];
-          double d[6];
-#pragma unroll
-          for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
-          if (R32)  // the sweep's residual, for an FP32 correction solve next round
-#pragma unroll
-            for (int q = 0; q < 6; q++) R32[base + (size_t)q * ld] = (float)d[q];
-          // squared change of |r| and |v| relative to the new iterate (one
-          // square root per trajectory, after the maximum)
-          double dr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-          double dv = d[3] * d[3] + d[4] * d[4] + d[5] * d[5];
-          if (s.relative) {
-            const double nr = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
-            const double nv = yn[3] * yn[3] + yn[4] * yn[4] + yn[5] * yn[5];
-            if (nr > 0.0) dr = dr / nr;
-            if (nv > 0.0) dv = dv / nv;
-          }
-          e2 = nanmax(e2, nanmax(dr, dv));
+          e2 = nanmax(e2, __shfl_xor_sync(0xffffffffu, e2, 1));
+          e2 = nanmax(e2, __shfl_xor_sync(0xffffffffu, e2, 2));
+          if (t == 0 && m >= 0) atomicMax(&emax_sh[tt], err_bits(e2));
         }
-      }
-      if (EPI == EPI_FULL || EPI == EPI_POS) {
-        e2 = nanmax(e2, __shfl_xor_sync(0xffffffffu, e2, 1));
-        e2 = nanmax(e2, __shfl_xor_sync(0xffffffffu, e2, 2));
-        if (t == 0 && m >= 0) atomicMax(&emax_sh[g], err_bits(e2));
       }
     }
     __syncthreads();
     // the tile holds every node of its trajectories: the maximum is final
-    if (tid < kSplitTraj) {
+    if (tid < TRAJ) {
       const int m = colm[tid];
       if ((EPI == EPI_FULL || EPI == EPI_POS) && m >= 0)
         c.err[m] = err_bits(sqrt(__longlong_as_double((long long)emax_sh[tid])));
@@ -265,18 +267,18 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
 template <int NC, int Q0, int EPI>
 cudaError_t split_attr(const pc_plan *p) {
   return cudaFuncSetAttribute(k_contract_split<NC, Q0, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)split_smem_bytes(p->split_ks, NC));
+                              (int)split_smem_bytes(p->split_ks));
 }
 
 template <int NC, int Q0, int EPI>
 void split_launch(const pc_plan *p, const Sweep &s, const Ctl &c, double *G, const double *Yold, double *Ynew,
                   float *R32, long long cols, cudaStream_t st) {
   SplitOp op{reinterpret_cast<const uint2 *>(p->d_Kdig), p->d_Kexp, p->split_nt, p->split_ks};
-  const long long tiles = (cols + kSplitTraj - 1) / kSplitTraj;
+  const long long tiles = (cols + split_traj(NC) - 1) / split_traj(NC);
   const int sms = p->num_sms > 0 ? p->num_sms : 152;
   const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((long long)sms * kSplitCtasPerSm, tiles));
-  k_contract_split<NC, Q0, EPI><<<blocks, kSplitThreads, split_smem_bytes(p->split_ks, NC), st>>>(s, c, op, G, Yold,
-                                                                                                 Ynew, R32);
+  k_contract_split<NC, Q0, EPI><<<blocks, kSplitThreads, split_smem_bytes(p->split_ks), st>>>(s, c, op, G, Yold, Ynew,
+                                                                                             R32);
 }
 
 }  // namespace
