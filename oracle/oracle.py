@@ -46,7 +46,8 @@ def build(force: bool = False) -> str:
 class _Model(C.Structure):
     _fields_ = [("n_bodies", C.c_int), ("mu_central", C.c_double), ("mu", C.POINTER(C.c_double)),
                 ("indirect", C.c_int), ("t_begin", C.c_double), ("granule", C.c_double),
-                ("degree", C.c_int), ("n_granules", C.c_int), ("coef", C.POINTER(C.c_double))]
+                ("degree", C.c_int), ("n_granules", C.c_int), ("coef", C.POINTER(C.c_double)),
+                ("c_light", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -81,6 +82,9 @@ def lib():
             L.ora_ephem_eval.argtypes = [P(_Model), C.c_double, P(C.c_double)]
             L.ora_accel.argtypes = [P(_Model), P(C.c_double), P(C.c_double), P(C.c_double)]
             L.ora_dynamics.argtypes = [P(_Model), P(_Opts), C.c_double, P(C.c_double), P(C.c_double)]
+            L.ora_eih_terms.argtypes = [C.c_int, P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double),
+                                        P(C.c_double), P(C.c_double), P(C.c_double), C.c_double, P(C.c_double)]
+            L.ora_eih_at.argtypes = [P(_Model), C.c_double, P(C.c_double), P(C.c_double)]
             L.ora_kepler.argtypes = [C.c_double, P(C.c_double), C.c_double, P(C.c_double)]
             L.ora_kepler.restype = C.c_int
             L.ora_pc_segment.argtypes = [P(_Model), P(_Opts), C.c_double, C.c_double, P(C.c_double),
@@ -126,6 +130,7 @@ class Model:
     granule: float = 1.0
     coef: np.ndarray | None = None      # [B][G][3][deg+1]
     indirect: bool = True
+    c_light: float = 0.0                # km/s; > 0 adds the EIH (1PN) terms
     _s: _Model = field(default=None, repr=False)
 
     def struct(self) -> _Model:
@@ -144,13 +149,15 @@ class Model:
         s.degree = int(self.coef.shape[3] - 1)
         s.n_granules = int(self.coef.shape[1])
         s.coef = _dp(self.coef)
+        s.c_light = float(self.c_light)
         self._s = s
         return s
 
     @staticmethod
-    def from_workload(w) -> "Model":
+    def from_workload(w, c_light: float = 0.0) -> "Model":
         return Model(mu_central=w.mu_central, mu=np.asarray(w.mu, dtype=np.float64), t_begin=w.t_begin,
-                     granule=w.granule, coef=np.asarray(w.coef, dtype=np.float64), indirect=w.indirect)
+                     granule=w.granule, coef=np.asarray(w.coef, dtype=np.float64), indirect=w.indirect,
+                     c_light=c_light)
 
 
 @dataclass
@@ -221,6 +228,25 @@ def dynamics(model: Model, opts: Opts, t: float, y) -> np.ndarray:
     f = np.zeros(6)
     lib().ora_dynamics(C.byref(s), C.byref(o), float(t), _dp(y), _dp(f))
     return f
+
+
+def eih_terms(mu, P, V, A, Phi, X, W, c: float) -> np.ndarray:
+    """The 1/c^2 EIH terms of a massless particle at X, W among explicit
+    bodies (mu [nb], P, V, A [nb][3], Phi [nb])."""
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    mu, P, V, A, Phi, X, W = map(f, (mu, P, V, A, Phi, X, W))
+    out = np.zeros(3)
+    lib().ora_eih_terms(int(mu.size), _dp(mu), _dp(P), _dp(V), _dp(A), _dp(Phi), _dp(X), _dp(W), float(c), _dp(out))
+    return out
+
+
+def eih_at(model: Model, t: float, y) -> np.ndarray:
+    """The model's EIH terms at t for the heliocentric state y."""
+    s = model.struct()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    out = np.zeros(3)
+    lib().ora_eih_at(C.byref(s), float(t), _dp(y), _dp(out))
+    return out
 
 
 def kepler(mu: float, x0, dt: float):

@@ -43,6 +43,12 @@
  *   ora_pc2_segment      pinned: constant acceleration exact, harmonic
  *                                oscillator closed form, same fixed point as
  *                                ora_pc_segment on a flyby-free segment
+ *   ora_eih_terms        pinned: Schwarzschild closed form (one body at rest),
+ *                                a body and a particle in uniform common motion
+ *                                (the boosted rest-frame field), perihelion
+ *                                advance 6 pi mu / (c^2 a (1 - e^2)); the terms
+ *                                in the bodies' accelerations (1/2 d.A, 7/2 A/r)
+ *                                are parity unpinned
  *   order 2 of ora_pc_segment / ora_propagate
  *                        pinned: bitwise ora_pc2_segment on a segment; same
  *                                fixed point as order 1 end to end; Gauss-
@@ -71,6 +77,7 @@ typedef struct {
   int degree;             /* Chebyshev degree of the table */
   int n_granules;
   const double *coef;     /* [n_bodies][n_granules][3][degree+1] */
+  double c_light;         /* speed of light, km/s: > 0 adds the EIH (1PN) terms; 0 Newtonian */
 } ora_model;
 
 /* Dynamics selector (the N-body model is the method's; the other two are the
@@ -256,13 +263,114 @@ void ora_accel(const ora_model *m, const double *rb, const double r[3], double a
   }
 }
 
-/* First-order dynamics f(y, t) = (v, a) of Eq. (ibvp). */
-static void ora_f(const ora_model *m, const ora_opts *o, const double *rb, const double y[6], double f[6]) {
+/* ------------------------------------------------------------------ */
+/* Einstein-Infeld-Hoffmann (1PN, beta = gamma = 1) terms of the         */
+/* acceleration of a massless particle at X with velocity W among nb    */
+/* point masses mu_j at P_j with velocities V_j, Newtonian accelerations */
+/* A_j and Newtonian potentials Phi_j = sum_{k != j} mu_k/|P_k - P_j|   */
+/* (the paper's force model, Section "Dynamics model", after the        */
+/* Explanatory Supplement).  With d_j = P_j - X, r_j = |d_j|, n_j =      */
+/* -d_j/r_j and phi = sum_j mu_j / r_j, the 1/c^2 part is               */
+/*   sum_j mu_j d_j/r_j^3 [ -4 phi - Phi_j + W.W + 2 V_j.V_j - 4 W.V_j   */
+/*                          - 3/2 (n_j.V_j)^2 + 1/2 d_j.A_j ] / c^2      */
+/* + sum_j mu_j/r_j^3 [ (-d_j).(4 W - 3 V_j) ] (W - V_j) / c^2           */
+/* + 7/2 sum_j mu_j A_j / r_j / c^2;                                     */
+/* the Newtonian part sum_j mu_j d_j/r_j^3 is not included.  Positions  */
+/* enter only as differences, velocities in the barycentric frame.     */
+/* ------------------------------------------------------------------ */
+void ora_eih_terms(int nb, const double *mu, const double *P, const double *V, const double *A, const double *Phi,
+                   const double X[3], const double W[3], double c, double out[3]) {
+  const double c2 = c * c;
+  double phi = 0.0;
+  for (int j = 0; j < nb; j++) {
+    const double d0 = P[3 * j] - X[0], d1 = P[3 * j + 1] - X[1], d2 = P[3 * j + 2] - X[2];
+    phi += mu[j] / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  }
+  const double ww = W[0] * W[0] + W[1] * W[1] + W[2] * W[2];
+  out[0] = out[1] = out[2] = 0.0;
+  for (int j = 0; j < nb; j++) {
+    const double *Pj = P + 3 * j, *Vj = V + 3 * j, *Aj = A + 3 * j;
+    const double d[3] = {Pj[0] - X[0], Pj[1] - X[1], Pj[2] - X[2]};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r = sqrt(r2), r3 = r2 * r;
+    const double vv = Vj[0] * Vj[0] + Vj[1] * Vj[1] + Vj[2] * Vj[2];
+    const double wv = W[0] * Vj[0] + W[1] * Vj[1] + W[2] * Vj[2];
+    const double nv = -(d[0] * Vj[0] + d[1] * Vj[1] + d[2] * Vj[2]) / r;
+    const double da = d[0] * Aj[0] + d[1] * Aj[1] + d[2] * Aj[2];
+    const double br = -4.0 * phi - Phi[j] + ww + 2.0 * vv - 4.0 * wv - 1.5 * nv * nv + 0.5 * da;
+    double sdot = 0.0;
+    for (int q = 0; q < 3; q++) sdot += -d[q] * (4.0 * W[q] - 3.0 * Vj[q]);
+    for (int q = 0; q < 3; q++)
+      out[q] += (mu[j] * d[q] / r3 * br + mu[j] / r3 * sdot * (W[q] - Vj[q]) + 3.5 * mu[j] * Aj[q] / r) / c2;
+  }
+}
+
+void ora_ephem_vel(const ora_model *m, double t, double *vb);
+
+/* EIH terms of the model at time t for the heliocentric state y: the Sun
+ * (body 0, at the heliocentric origin) and the table's bodies, velocities
+ * shifted to the barycentre by V_S = -sum_b mu_b v_b / (mu_S + sum_b mu_b),
+ * Newtonian accelerations and potentials of every body from the others.
+ * Added to the Newtonian heliocentric acceleration (which already carries the
+ * Sun's Newtonian acceleration as the indirect term) this is the barycentric
+ * EIH acceleration minus the Sun's Newtonian barycentric acceleration. */
+static void ora_eih_model(const ora_model *m, double t, const double *rb, const double y[6], double out[3]) {
+  const int B = m->n_bodies, nb = B + 1;
+  double mu[33], P[99], V[99], A[99], Phi[33], vb[96];
+  if (B > 0) ora_ephem_vel(m, t, vb);
+  double msum = m->mu_central, vs[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < B; b++) {
+    msum += m->mu[b];
+    for (int q = 0; q < 3; q++) vs[q] -= m->mu[b] * vb[3 * b + q];
+  }
+  for (int q = 0; q < 3; q++) vs[q] /= msum;
+  mu[0] = m->mu_central;
+  for (int q = 0; q < 3; q++) {
+    P[q] = 0.0;
+    V[q] = vs[q];
+  }
+  for (int b = 0; b < B; b++) {
+    mu[b + 1] = m->mu[b];
+    for (int q = 0; q < 3; q++) {
+      P[3 * (b + 1) + q] = rb[3 * b + q];
+      V[3 * (b + 1) + q] = vb[3 * b + q] + vs[q];
+    }
+  }
+  for (int j = 0; j < nb; j++) {
+    Phi[j] = 0.0;
+    for (int q = 0; q < 3; q++) A[3 * j + q] = 0.0;
+    for (int k = 0; k < nb; k++) {
+      if (k == j) continue;
+      const double d[3] = {P[3 * k] - P[3 * j], P[3 * k + 1] - P[3 * j + 1], P[3 * k + 2] - P[3 * j + 2]};
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r = sqrt(r2);
+      Phi[j] += mu[k] / r;
+      for (int q = 0; q < 3; q++) A[3 * j + q] += mu[k] * d[q] / (r2 * r);
+    }
+  }
+  const double W[3] = {y[3] + vs[0], y[4] + vs[1], y[5] + vs[2]};
+  ora_eih_terms(nb, mu, P, V, A, Phi, y, W, m->c_light, out);
+}
+
+/* Public: the model's EIH terms at t (tests). */
+void ora_eih_at(const ora_model *m, double t, const double y[6], double out[3]) {
+  double rb[96];
+  if (m->n_bodies > 0) ora_ephem_eval(m, t, rb);
+  ora_eih_model(m, t, rb, y, out);
+}
+
+/* First-order dynamics f(y, t) = (v, a) of Eq. (ibvp); rb holds the bodies'
+ * positions at t. */
+static void ora_f(const ora_model *m, const ora_opts *o, double t, const double *rb, const double y[6],
+                  double f[6]) {
   f[0] = y[3];
   f[1] = y[4];
   f[2] = y[5];
   if (o->dyn == ORA_DYN_NBODY) {
     ora_accel(m, rb, y, f + 3);
+    if (m->c_light > 0.0) {
+      double e[3];
+      ora_eih_model(m, t, rb, y, e);
+      for (int q = 0; q < 3; q++) f[3 + q] += e[q];
+    }
   } else if (o->dyn == ORA_DYN_CONST_ACCEL) {
     f[3] = o->dyn_param[0];
     f[4] = o->dyn_param[1];
@@ -281,7 +389,7 @@ void ora_dynamics(const ora_model *m, const ora_opts *o, double t, const double 
     rb = (double *)malloc(sizeof(double) * 3 * m->n_bodies);
     ora_ephem_eval(m, t, rb);
   }
-  ora_f(m, o, rb, y, f);
+  ora_f(m, o, t, rb, y, f);
   free(rb);
 }
 
@@ -470,7 +578,7 @@ static int ora_pc_segment_core(const ora_model *m, const ora_opts *o, const doub
   ora_stop_state st = {INFINITY, 0};
   int outcome = ORA_SEG_FAIL_CAP, i;
   for (i = 1; i <= o->max_iters; i++) {
-    for (int j = 0; j < n; j++) ora_f(m, o, B ? ephem + (size_t)j * B * 3 : NULL, Y + 6 * j, G + 6 * j);
+    for (int j = 0; j < n; j++) ora_f(m, o, tj[j], B ? ephem + (size_t)j * B * 3 : NULL, Y + 6 * j, G + 6 * j);
     if (o->order == 2) {
       /* second-order form: velocities from the integrated accelerations, then
          positions from the integrated new velocities (as ora_pc2_segment) */
@@ -785,7 +893,7 @@ int ora_gl_propagate(const ora_model *m, const ora_opts *o, int s, const double 
     const double tn = t0 + (double)st * h;
     if (B) ora_ephem_eval(m, tn, rb);
     double f0[6];
-    ora_f(m, o, rb, y, f0);
+    ora_f(m, o, tn, rb, y, f0);
     for (int i = 0; i < s; i++)
       for (int q = 0; q < 6; q++) Kst[i][q] = f0[q];
     int it;
@@ -798,7 +906,7 @@ int ora_gl_propagate(const ora_model *m, const ora_opts *o, int s, const double 
           ys[q] = y[q] + h * acc;
         }
         if (B) ora_ephem_eval(m, tn + c[i] * h, rb);
-        ora_f(m, o, rb, ys, Kn[i]);
+        ora_f(m, o, tn + c[i] * h, rb, ys, Kn[i]);
       }
       for (int i = 0; i < s; i++)
         for (int q = 0; q < 6; q++) {
@@ -1148,7 +1256,7 @@ int ora_pc2_segment(const ora_model *m, const ora_opts *o, double ta, double tb,
   for (i = 1; i <= o->max_iters; i++) {
     for (int j = 0; j < n; j++) {
       double f[6];
-      ora_f(m, o, B ? eph + (size_t)j * B * 3 : NULL, Y + 6 * j, f);
+      ora_f(m, o, w1 + w2 * tau[j], B ? eph + (size_t)j * B * 3 : NULL, Y + 6 * j, f);
       for (int c = 0; c < 3; c++) A[3 * j + c] = f[3 + c];
     }
     for (int j = 0; j < n; j++)      /* velocities from the accelerations */
