@@ -10,7 +10,10 @@ pc_propagate call over all of them.  The mixed-precision batched path (FP32
 sweeps until the change is below 1e-6, then FP64 sweeps with FP32 correction
 solves, to 1e-13) is the line's value; the plain FP64 GPU sweep runs on the
 same inputs, timed the same way (same steps, graph replay, no per-kernel
-instrumentation), in stats.plain_fp64.  Every step runs the whole hot path on
+instrumentation), in stats.plain_fp64.  Both arms use the second-order form
+of the sweep (--order 1: the paper's first-order sweep) and the FP64
+contraction by exact digit products on the bf16 tensor cores (--contraction
+dmma: on the FP64 tensor cores).  Every step runs the whole hot path on
 the GPU: per-trajectory segment schedule, ephemeris at the nodes, Keplerian
 warm start, force, operator contraction, convergence tests, stitching.
 
@@ -161,13 +164,14 @@ def shard(n_total: int, world: int, rank: int):
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_rate(w, n_sample: int, threads: int):
-    """Times the CPU oracle on the first n_sample trajectories; returns (traj/s, seconds)."""
+def oracle_rate(w, n_sample: int, threads: int, order: int = 1):
+    """Times the CPU oracle on the first n_sample trajectories, with the sweep
+    of the given order; returns (traj/s, seconds)."""
     from oracle import oracle as ora
     ora.build()
     m = ora.Model.from_workload(w)
     o = ora.Opts(N=w.N, segments=w.segments, seg_mode=w.seg_mode, tol=w.tol, max_iters=w.max_iters,
-                 max_depth=w.max_depth)
+                 max_depth=w.max_depth, order=order)
     x = w.x0[:n_sample]
     t = time.perf_counter()
     ora.propagate(m, o, x, w.t0, w.tf, threads=threads)
@@ -183,9 +187,11 @@ def headline_workload(args, n_total):
     return W.config2(M=n_total, years=args.years)
 
 
-def cpu_sample_note(w, n, secs, cores):
+def cpu_sample_note(w, n, secs, cores, order=1):
     arc = "2-year" if w.name.startswith("cfg3") else f"{(w.tf - w.t0) / 31557600.0:g}-year"
-    return f"seeded subset: first {n} of the workload's trajectories, full {arc} arcs, {secs:.1f} s on {cores} threads"
+    kind = "second-order" if order == 2 else "first-order"
+    return (f"seeded subset: first {n} of the workload's trajectories, full {arc} arcs, {kind} sweeps, "
+            f"{secs:.1f} s on {cores} threads")
 
 
 def run_reference(args, world, rank):
@@ -196,14 +202,14 @@ def run_reference(args, world, rank):
     w = headline_workload(args, IC_PER_RANK[args.workload])
     n_sample = args.ref_sample or (1024 if args.workload == "precision" else 128)
     for _ in range(args.warmup):
-        oracle_rate(w, max(cores, n_sample // 8), cores)
+        oracle_rate(w, max(cores, n_sample // 8), cores, args.order)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_rate(w, n_sample, cores)
+        _, dt = oracle_rate(w, n_sample, cores, args.order)
         times.append(dt)
     ms = 1000.0 * sum(times) / len(times)
     value = n_sample / (ms / 1000.0)
-    sample = cpu_sample_note(w, n_sample, ms / 1000.0, cores) + " per step"
+    sample = cpu_sample_note(w, n_sample, ms / 1000.0, cores, args.order) + " per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -501,7 +507,8 @@ def run_ours(args, world, rank, local):
             "config": {"workload": w.name, "n_ic_per_gpu": M, "N": w.N,
                        "arc_years": round((w.tf - w.t0) / 31557600.0, 3), "tol": w.tol,
                        "path": ("mixed FP32->FP64 batched sweep" if mixed else "plain FP64 batched sweep")
-                               + " (per-trajectory segments, compaction, DMMA contraction)",
+                               + " (per-trajectory segments, compaction, "
+                               + ("second-order" if args.order == 2 else "first-order") + " sweeps)",
                        "switch_tol": switch_tol if mixed else None,
                        "sweep_order": args.order,
                        "fp64_contraction": ("exact 8-bit digit products on the bf16 tensor cores"
@@ -660,8 +667,8 @@ def main(argv=None):
     ap.add_argument("--switch-tol", type=float, default=None,
                     help="FP32 -> FP64 switch threshold (default 1e-6 precision, 0 flyby: when the FP32 change "
                          "stops falling)")
-    ap.add_argument("--order", type=int, choices=[1, 2], default=1,
-                    help="1: the paper's sweep; 2: its second-order form (both arms)")
+    ap.add_argument("--order", type=int, choices=[1, 2], default=2,
+                    help="1: the paper's sweep; 2: its second-order form (both arms; the default)")
     ap.add_argument("--contraction", choices=["split", "dmma"], default="split",
                     help="FP64 contraction: exact digit products on the bf16 tensor cores, or the FP64 tensor cores")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")

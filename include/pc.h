@@ -72,6 +72,14 @@ typedef struct {
   double mu_central;   /* GM of the central body, > 0 */
   const double *mu;    /* host [n_bodies], copied at plan creation */
   int indirect;        /* 1: include the indirect term */
+  double c_light;      /* speed of light in km/s: > 0 adds the relativistic terms of the
+                          Einstein-Infeld-Hoffmann equations (the paper's model, Section
+                          "Dynamics model"): for the particle among the central body and the
+                          table's bodies, velocities taken in the barycentric frame, each body's
+                          Newtonian acceleration and potential from the others; 0: Newtonian.
+                          The FP32 sweeps of mixed precision keep the Newtonian terms (the FP64
+                          sweeps and their residual carry the relativistic ones); reverse mode
+                          (tape, adjoint) refuses such a plan with PC_EINVAL. */
 } pc_force_model;
 
 /* Ephemeris: granule g covers [t_begin + g*granule_s, t_begin + (g+1)*granule_s)

@@ -493,7 +493,8 @@ using namespace pcx;
 extern "C" pc_status pc_propagate_tape(pc_plan *p, long long n_ic, const double *x0, const double *t0,
                                        const double *tf, const int *segments, double tol, double *xf, int *status,
                                        int *nseg, int max_seg, double *tape, void *stream) {
-  if (!p || n_ic < 0) return PC_EINVAL;
+  // reverse mode differentiates the Newtonian force only
+  if (!p || n_ic < 0 || p->model.c_light > 0.0) return PC_EINVAL;
   if (n_ic == 0) return PC_OK;
   if (!x0 || !t0 || !tf || !xf || !nseg || !tape || max_seg < 1 || n_ic > (1LL << 30)) return PC_EINVAL;
   return propagate_with_tape(p, n_ic, x0, 0.0, 0.0, t0, tf, segments, tol, xf, status, nullptr, nseg, max_seg, tape,
@@ -503,7 +504,8 @@ extern "C" pc_status pc_propagate_tape(pc_plan *p, long long n_ic, const double 
 extern "C" pc_status pc_adjoint_tape(pc_plan *p, long long n_ic, const int *nseg, int max_seg, const double *tape,
                                      const double *xf_bar, double tol, double *x0_bar, int *status, int *iters,
                                      void *stream) {
-  if (!p || n_ic < 0) return PC_EINVAL;
+  // reverse mode differentiates the Newtonian force only
+  if (!p || n_ic < 0 || p->model.c_light > 0.0) return PC_EINVAL;
   if (n_ic == 0) return PC_OK;
   if (!nseg || !tape || !xf_bar || !x0_bar || max_seg < 1 || n_ic > (1LL << 30)) return PC_EINVAL;
   const int T = adjoint_tile(p);
@@ -586,7 +588,8 @@ extern "C" pc_status pc_adjoint_tape(pc_plan *p, long long n_ic, const int *nseg
 
 extern "C" pc_status pc_propagate_adjoint(pc_plan *p, long long n_ic, const double *x0, double t0, double tf,
                                           double tol, const double *xf_bar, double *x0_bar, void *stream) {
-  if (!p || n_ic < 0) return PC_EINVAL;
+  // reverse mode differentiates the Newtonian force only
+  if (!p || n_ic < 0 || p->model.c_light > 0.0) return PC_EINVAL;
   if (n_ic == 0) return PC_OK;
   if (!x0 || !xf_bar || !x0_bar || n_ic > (1LL << 30)) return PC_EINVAL;
   pc_status ps = ensure_adjoint_workspace(p, n_ic);

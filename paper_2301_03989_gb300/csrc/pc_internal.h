@@ -71,7 +71,12 @@ struct Model {
   double t_begin, granule;
   int deg, n_gr;
   const double *coef; // [B][n_gr][3][deg+1]
+  double c_light;     // > 0: Einstein-Infeld-Hoffmann terms in the FP64 force
 };
+// Per node, with the EIH terms: for the central body (0) and each table body
+// (1..B) its barycentric velocity (3), Newtonian acceleration (3) and
+// potential (1) from the other bodies.
+__host__ __device__ constexpr int eih_stride(int B) { return 7 * (B + 1); }
 
 // Per-trajectory control state, structure of arrays of length ld, indexed by
 // slot.  Active trajectories are packed into slots [0, A); ic[slot] is the
@@ -154,6 +159,7 @@ struct Workspace {
   double *tails = nullptr;   // [ceil(n/8)][14][ld] resolution-test partial sums of the round's FP64 sweeps
   double *E[2] = {nullptr, nullptr};    // [n][B][3][ld] body positions at the nodes (+ repack target)
   double *Aind[2] = {nullptr, nullptr}; // [n][3][ld] summed indirect acceleration (+ repack target)
+  double *EX[2] = {nullptr, nullptr};   // [n][eih_stride(B)][ld] bodies' EIH data (c_light > 0; + repack target)
   // mixed precision (allocated when the plan asks for it), by new-segment list entry
   double *YK = nullptr;      // [entry][n][6] FP64 warm start
   double *YK17 = nullptr;    // [17][6][ld] Kepler solutions at the interpolation nodes, by new-segment entry

@@ -108,7 +108,8 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
   *out = nullptr;
   if (N < 2 || N > kMaxN || segments < 1 || !force) return PC_EINVAL;
   const int B = force->n_bodies;
-  if (B < 0 || B > kMaxBodies || !(force->mu_central > 0.0) || (B > 0 && !force->mu)) return PC_EINVAL;
+  if (B < 0 || B > kMaxBodies || !(force->mu_central > 0.0) || (B > 0 && !force->mu) || !(force->c_light >= 0.0))
+    return PC_EINVAL;
   if (B > 0) {
     if (!ephem || ephem->n_bodies != B || !(ephem->granule_s > 0.0) || ephem->degree < 0 || ephem->degree > 63 ||
         ephem->n_granules < 1 || !ephem->coef)
@@ -253,6 +254,7 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
   m.B = B;
   m.mu_c = force->mu_central;
   m.indirect = force->indirect ? 1 : 0;
+  m.c_light = force->c_light;
   if (B > 0) {
     m.t_begin = ephem->t_begin;
     m.granule = ephem->granule_s;
@@ -335,6 +337,7 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic, int mixed) {
     if (B > 0) e = dalloc(&w.E[b], n * B * 3 * ld);
     if (e == cudaSuccess) e = dalloc(&w.Aind[b], n * 3 * ld);
     if (e == cudaSuccess) e = cudaMemset(w.Aind[b], 0, sizeof(double) * n * 3 * ld);
+    if (e == cudaSuccess && p->model.c_light > 0.0) e = dalloc(&w.EX[b], n * (size_t)eih_stride((int)B) * ld);
     if (e == cudaSuccess) e = cudaMalloc(&w.ctl_block[b], ctl_bytes);
     if (e == cudaSuccess) e = cudaMemset(w.ctl_block[b], 0, ctl_bytes);
   }
@@ -370,6 +373,7 @@ void pcx::free_workspace(pc_plan *p) {
     cudaFree(w.Y[b]);
     cudaFree(w.E[b]);
     cudaFree(w.Aind[b]);
+    cudaFree(w.EX[b]);
     cudaFree(w.ctl_block[b]);
   }
   cudaFree(w.YK);

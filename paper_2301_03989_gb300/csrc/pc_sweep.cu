@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(32 * kForceNodes) k_force(Sweep s, Ctl c, Mode
                                                           const double *__restrict__ E,
                                                           const double *__restrict__ Aind, double *__restrict__ G,
                                                           const double *__restrict__ tau,
-                                                          double *__restrict__ partials) {
+                                                          double *__restrict__ partials,
+                                                          const double *__restrict__ EX) {
   __shared__ double red[kForceNodes][kTailVals][32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * 32 + tx;
@@ -463,6 +464,12 @@ __global__ void __launch_bounds__(32 * kForceNodes) k_force(Sweep s, Ctl c, Mode
     for (int q = 0; q < 6; q++) y[q] = Y[yb + (size_t)q * ld];
     double a[3];
     accel(md, E + (size_t)j * md.B * 3 * ld + m, Aind + (size_t)j * 3 * ld + m, (size_t)ld, y, a);
+    if (md.c_light > 0.0) {  // Einstein-Infeld-Hoffmann terms
+      double e3[3];
+      eih_terms(md, E + (size_t)j * md.B * 3 * ld + m, EX + (size_t)j * eih_stride(md.B) * ld + m, (size_t)ld, y,
+                y + 3, e3);
+      for (int q = 0; q < 3; q++) a[q] += e3[q];
+    }
     const double g[6] = {w2 * y[3], w2 * y[4], w2 * y[5], w2 * a[0], w2 * a[1], w2 * a[2]};
 #pragma unroll
     for (int q = 0; q < 6; q++) G[yb + (size_t)q * ld] = g[q];
@@ -1653,9 +1660,47 @@ __global__ void k_eval_dyn(Model md, long long n, const double *__restrict__ t, 
   const double r[3] = {y[i], y[n + i], y[2 * n + i]};
   double a[3];
   accel(md, rb, ind, 1, r, a);
+  if (md.c_light > 0.0) {
+    double vb[kMaxBodies * 3], X[7 * (kMaxBodies + 1)], e3[3];
+    ephem_vel_all(md, L, [&](int b, const double v[3]) {
+      for (int ax = 0; ax < 3; ax++) vb[3 * b + ax] = v[ax];
+    });
+    eih_bodies(md, rb, vb, X);
+    const double v[3] = {y[3 * n + i], y[4 * n + i], y[5 * n + i]};
+    eih_terms(md, rb, X, 1, r, v, e3);
+    for (int q = 0; q < 3; q++) a[q] += e3[q];
+  }
   for (int q = 0; q < 3; q++) {
     f[q * n + i] = y[(3 + q) * n + i];
     f[(3 + q) * n + i] = a[q];
+  }
+}
+
+// EIH data of the bodies at the nodes of the new segments (grid-stride over
+// list entries x nodes, entries fastest, as k_setup): EX[j][f][slot] with the
+// layout of eih_bodies.
+__global__ void k_setup_eih(Sweep s, Ctl c, Model md, const double *__restrict__ tau, double *__restrict__ EX) {
+  const int cur = s.list_cur;
+  const long long count = s.list_cnt[cur];
+  const int *__restrict__ list = s.list[cur];
+  const long long total = count * s.n;
+  const int ld = s.ld, B = md.B, xs = eih_stride(B);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / count);
+    const long long e = i - (long long)j * count;
+    const int m = list[e];
+    const double t = dadd(c.w1[m], dmul(c.w2[m], tau[j]));
+    const EphemLoc L = ephem_locate(md, t);
+    double rb[kMaxBodies * 3], vb[kMaxBodies * 3], X[7 * (kMaxBodies + 1)];
+    ephem_all(md, L, [&](int b, const double r[3]) {
+      for (int ax = 0; ax < 3; ax++) rb[3 * b + ax] = r[ax];
+    });
+    ephem_vel_all(md, L, [&](int b, const double v[3]) {
+      for (int ax = 0; ax < 3; ax++) vb[3 * b + ax] = v[ax];
+    });
+    eih_bodies(md, rb, vb, X);
+    for (int f = 0; f < xs; f++) EX[((size_t)j * xs + f) * ld + m] = X[f];
   }
 }
 
@@ -1823,6 +1868,10 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
     p->acc_launches += 1;
   }
   k_setup<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->model, p->d_tau, Yc, E, Ai, mx);
+  if (p->model.c_light > 0.0) {
+    k_setup_eih<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->model, p->d_tau, w.EX[w.live]);
+    p->acc_launches += 1;
+  }
   if (ev) cudaEventRecord(ev[1], st);
   float *R32 = s.refine ? w.R32[w.live] : nullptr;
   if (s.mixed) launch_fp32<FP32_KEPLER>(p, s, Yc, Yn, E, R32, mx, sb);
@@ -1837,7 +1886,7 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
   }
   if (ev) cudaEventRecord(ev[2], st);
   k_force<<<dim3(blocks_for(s.A, 32), (s.n + kForceNodes - 1) / kForceNodes), dim3(32, kForceNodes), 0, st>>>(
-      s, c, p->model, Yc, E, Ai, w.G, p->d_tau, w.tails);
+      s, c, p->model, Yc, E, Ai, w.G, p->d_tau, w.tails, w.EX[w.live]);
   if (ev) cudaEventRecord(ev[3], st);
   if (use_split(p)) {
     // exact digit products on the bf16 tensor cores
@@ -1878,9 +1927,11 @@ cudaError_t launch_repack(const pc_plan *p, const Sweep &s, int cur, cudaStream_
   k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 6, w.pos, w.Y[cur], w.Y[cur ^ 1]);
   if (B > 0) k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * B * 3, w.pos, w.E[a], w.E[b]);
   k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 3, w.pos, w.Aind[a], w.Aind[b]);
+  if (w.EX[a])
+    k_repack_rows<double><<<g, kThreads, 0, st>>>(s.A, s.ld, n * eih_stride((int)B), w.pos, w.EX[a], w.EX[b]);
   if (s.refine) k_repack_rows<float><<<g, kThreads, 0, st>>>(s.A, s.ld, n * 6, w.pos, w.R32[a], w.R32[b]);
   k_repack_ctl<<<nb, kThreads, 0, st>>>(s, w.ctl[a], w.ctl[b], w.pos);
-  p->acc_launches += 4 + (B > 0) + (s.refine ? 1 : 0);
+  p->acc_launches += 4 + (B > 0) + (s.refine ? 1 : 0) + (w.EX[a] ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ class PCError(RuntimeError):
 
 class ForceModel(C.Structure):
     _fields_ = [("n_bodies", C.c_int), ("mu_central", C.c_double), ("mu", C.POINTER(C.c_double)),
-                ("indirect", C.c_int)]
+                ("indirect", C.c_int), ("c_light", C.c_double)]
 
 
 class Ephemeris(C.Structure):
@@ -175,10 +175,12 @@ class Plan:
 
 
 def plan_create(N: int, segments: int, mu_central: float, mu, t_begin: float = 0.0, granule: float = 1.0,
-                coef=None, indirect: bool = True, options: Options | None = None) -> Plan:
+                coef=None, indirect: bool = True, options: Options | None = None, c_light: float = 0.0) -> Plan:
+    """c_light > 0 (km/s) adds the Einstein-Infeld-Hoffmann terms to the force."""
     mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64).reshape(-1))
     B = int(mu.size)
-    fm = ForceModel(B, float(mu_central), mu.ctypes.data_as(C.POINTER(C.c_double)) if B else None, int(bool(indirect)))
+    fm = ForceModel(B, float(mu_central), mu.ctypes.data_as(C.POINTER(C.c_double)) if B else None, int(bool(indirect)),
+                    float(c_light))
     eph_p = None
     if B:
         coef = np.ascontiguousarray(np.asarray(coef, dtype=np.float64))
@@ -193,11 +195,11 @@ def plan_create(N: int, segments: int, mu_central: float, mu, t_begin: float = 0
     return Plan(h.value, int(N))
 
 
-def plan_from_workload(w, **opts) -> Plan:
+def plan_from_workload(w, c_light: float = 0.0, **opts) -> Plan:
     o = options_default(tol=w.tol, max_iters=w.max_iters, max_depth=w.max_depth, seg_mode=w.seg_mode)
     for k, v in opts.items():
         setattr(o, k, v)
-    return plan_create(w.N, w.segments, w.mu_central, w.mu, w.t_begin, w.granule, w.coef, w.indirect, o)
+    return plan_create(w.N, w.segments, w.mu_central, w.mu, w.t_begin, w.granule, w.coef, w.indirect, o, c_light=c_light)
 
 
 def propagate(plan: Plan, x0, t0: float, tf: float, xf, tol: float = 0.0, status=None, iters=None, stream=None,

@@ -54,6 +54,8 @@ def test_argument_errors_without_a_gpu():
     assert L.pc_plan_create(64, 4, C.byref(fm), None, None, None) == E                 # no output
     bad = pc.ForceModel(2, 1.0, None, 1)                                                # bodies without GMs
     assert L.pc_plan_create(64, 4, C.byref(bad), None, None, C.byref(out)) == E
+    bad = pc.ForceModel(0, 1.0, None, 1, -1.0)                                          # negative speed of light
+    assert L.pc_plan_create(64, 4, C.byref(bad), None, None, C.byref(out)) == E
     o = pc.options_default(precision=pc.PC_PREC_MIXED)
     assert L.pc_plan_create(300, 4, C.byref(fm), None, C.byref(o), C.byref(out)) == E  # mixed needs N <= 287
     o = pc.options_default(refine32=2)
