@@ -470,11 +470,11 @@ def run_ours(args, world, rank, local):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             n_cpu = min(M, args.cpu_sample or (4096 if args.workload == "precision" else 256))
-            rate, secs = oracle_rate(w, n_cpu, cores)
+            rate, secs = oracle_rate(w, n_cpu, cores, args.order)
             n1 = min(M, max(1, n_cpu // 16))
-            rate1, secs1 = oracle_rate(w, n1, 1)
+            rate1, secs1 = oracle_rate(w, n1, 1, args.order)
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": cpu_sample_note(w, n_cpu, secs, cores),
+                   "sample": cpu_sample_note(w, n_cpu, secs, cores, args.order),
                    "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                                      "sample": f"first {n1} trajectories, {secs1:.1f} s"}}
         stats = {"sweep_rounds_per_step": rounds_total / max(1, args.steps),

@@ -281,7 +281,11 @@ pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
  *                         kernel (4 or 8), or 0 for one trajectory per CTA
  *   fp32_slots            FP32 kernels: trajectories per CTA of the tiled kernel
  *                         (8..64, a multiple of 8; fewer when N is large)
- * Defaults: 4, 1, 4, 8, 8, 1, 1, 8, 16.  Profiling (pc_plan_set_profiling)
+ *   grid_cache            1: the body positions at the nodes of a round's new
+ *                         segments are evaluated once per distinct node-time grid
+ *                         (segments with the same start and length share one) and
+ *                         copied; 0: evaluated for every segment
+ * Defaults: 4, 1, 4, 8, 8, 1, 1, 8, 16, 1.  Profiling (pc_plan_set_profiling)
  * launches directly whatever `graphs` says. */
 typedef struct {
   int setup_ctas_per_sm;
@@ -293,6 +297,7 @@ typedef struct {
   int side_priority;
   int fp32_rows;
   int fp32_slots;
+  int grid_cache;
 } pc_tuning;
 
 /* Reads / replaces the plan's tuning (PC_EINVAL on a value out of range). */

@@ -106,6 +106,16 @@ pc_status session_begin(Session &S, pc_plan *p, long long n_ic, long long io_ld,
   s.kep_stride = p->kep_stride;
   s.Lint = p->d_Lint;
   s.YK17 = w.YK17;
+  s.eh_size = (w.EC && p->tune.grid_cache) ? w.eh_size : 0;
+  s.eh_cap = w.eh_cap;
+  s.eh_tab[0] = w.eh_tab;
+  s.eh_tab[1] = w.eh_tab + w.eh_size;
+  s.eh_uid[0] = w.eh_tab + 2 * (size_t)w.eh_size;
+  s.eh_uid[1] = w.eh_tab + 3 * (size_t)w.eh_size;
+  s.eh_ent = w.eh_ent;
+  s.eh_own = w.eh_own;
+  s.eh_cnt = w.ints + 13;
+  s.EC = w.EC;
   s.cnt64 = w.cnt64;
   s.list_cur = 0;
   s.A = (int)n_ic;
@@ -484,7 +494,7 @@ extern "C" pc_status pc_plan_set_tuning(pc_plan *p, const pc_tuning *t) {
       t->rounds_per_batch > 64 || t->repack_div < 2 || t->repack_div > 64 || (t->graphs != 0 && t->graphs != 1) ||
       (t->side_priority != 0 && t->side_priority != 1) ||
       (t->fp32_rows != 0 && t->fp32_rows != 4 && t->fp32_rows != 8) || t->fp32_slots < 8 || t->fp32_slots > 64 ||
-      t->fp32_slots % 8 != 0)
+      t->fp32_slots % 8 != 0 || (t->grid_cache != 0 && t->grid_cache != 1))
     return PC_EINVAL;
   p->tune = *t;
   return PC_OK;
@@ -546,6 +556,7 @@ extern "C" pc_status pc_plan_autotune(pc_plan *p, long long n_ic, const double *
   axis(&pc_tuning::rounds_per_batch, {4, 8, 16, 32});
   axis(&pc_tuning::repack_div, {4, 8, 16});
   axis(&pc_tuning::graphs, {0, 1});
+  if (p->model.B > 0) axis(&pc_tuning::grid_cache, {0, 1});
   for (const Move &mv : moves) {
     if (ps != PC_OK) break;
     pc_tuning cand = cur;

@@ -106,8 +106,20 @@ struct Sweep {
   int N, n, kpad, rows_pad;  // degree, nodes, padded k extent, padded output rows (nodes 1..N)
   int order;                 // 1: the paper's sweep; 2: its second-order form
   int kep_stride;            // warm start solved at nodes 0, kep_stride, ..., N (0: at every node)
-  const double *Lint;        // [n][17] interpolation weights (kep_stride > 0)
-  double *YK17;              // [17][6][ld] Kepler solutions at those nodes
+  const float *Lint;         // [2][n][17] interpolation weights (kep_stride > 0) as FP32 pairs hi + lo
+  float *YK17;               // [2][17][6][ld] Kepler solutions at those nodes minus the start state,
+                             // as FP32 pairs hi + lo
+  // Ephemeris of the round's new segments, evaluated once per distinct node-
+  // time grid (w1, w2): an open-addressing table per round parity maps a grid
+  // to its owning list entry and its index u in the cache EC.
+  int eh_size;               // table slots, a power of two >= 2 ld (0: no cache)
+  int eh_cap;                // grids the cache holds; grids beyond it are evaluated per entry
+  int *eh_tab[2];            // [eh_size] owning list entry, -1 when free
+  int *eh_uid[2];            // [eh_size] the owner's grid index u, -1 beyond eh_cap
+  int *eh_ent;               // [ld] table slot of each list entry (-1: none)
+  int *eh_own;               // [eh_cap] owning list entry of grid u
+  int *eh_cnt;               // [2] grids of the round, by parity (cleared by the set-up kernel)
+  double *EC;                // [n][3B + 3][eh_cap] body positions and summed indirect term by grid
   long long n_ic;
   int ld;                    // leading dimension over slots (multiple of 8)
   int A;                     // slots [0, A) may hold active trajectories
@@ -162,7 +174,15 @@ struct Workspace {
   double *EX[2] = {nullptr, nullptr};   // [n][eih_stride(B)][ld] bodies' EIH data (c_light > 0; + repack target)
   // mixed precision (allocated when the plan asks for it), by new-segment list entry
   double *YK = nullptr;      // [entry][n][6] FP64 warm start
-  double *YK17 = nullptr;    // [17][6][ld] Kepler solutions at the interpolation nodes, by new-segment entry
+  float *YK17 = nullptr;     // [2][17][6][ld] Kepler deviations at the interpolation nodes (FP32 pairs),
+                             // by new-segment entry
+  // per-round ephemeris cache (model with bodies): tables by parity, per-entry
+  // slots, grid owners and the cache itself
+  int eh_size = 0, eh_cap = 0;
+  int *eh_tab = nullptr;     // [2][eh_size] owners, then [2][eh_size] grid indices
+  int *eh_ent = nullptr;     // [ld]
+  int *eh_own = nullptr;     // [eh_cap]
+  double *EC = nullptr;      // [n][3B + 3][eh_cap]
   float *X32 = nullptr;      // [entry][n][x32_stride(B)] FP32 node records
   float *R32[2] = {nullptr, nullptr};   // [n][6][ld] FP64 sweep residual Y' - Y, rounded (+ repack target)
   Ctl ctl[2]{};              // live control state and repack target
@@ -171,7 +191,8 @@ struct Workspace {
   int *ints = nullptr;       // [0..1] done counters [finished, stopped], [2..3] setup list counts,
                              // [4] repack count, [5..6] FP64 list counts, [7] tile counter,
                              // [8..9] correction list counts, [10..11] FP32 list-entry counters,
-                             // [12] tile counter of the second-order position pass
+                             // [12] tile counter of the second-order position pass,
+                             // [13..14] ephemeris-cache grid counts
   int *pos = nullptr;        // [ld] repack destinations
   unsigned long long *cnt64 = nullptr;  // [0] FP64 trajectory-sweeps, [1] FP32 trajectory-sweeps
   unsigned long long *h_cnt64 = nullptr;
@@ -205,7 +226,7 @@ struct pc_plan {
   int N = 0, n = 0, kpad = 0, rows_pad = 0;
   int segments = 0;
   pc_options opt{};
-  pc_tuning tune{4, 1, 4, 8, 8, 1, 1, 8, 16};
+  pc_tuning tune{4, 1, 4, 8, 8, 1, 1, 8, 16, 1};
   long long session_id = 0;  // distinguishes calls for the graph cache
   int device = 0;
   // model (device copies)
@@ -224,7 +245,7 @@ struct pc_plan {
   // nodes of the embedded degree-16 Chebyshev-Lobatto grid), the other nodes
   // interpolated with d_Lint [N+1][17]; kep_stride 0: solved at every node
   int kep_stride = 0;
-  double *d_Lint = nullptr;
+  float *d_Lint = nullptr;
   unsigned *d_Kdig = nullptr;
   int *d_Kexp = nullptr;
   int split_nt = 0, split_ks = 0;   // ceil(N/8) node tiles, ceil((N+1)/16) k-steps

@@ -168,14 +168,15 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
     if (e == cudaSuccess) e = cudaMemcpy(p->d_K32R, Kr.data(), sizeof(float) * Kr.size(), cudaMemcpyHostToDevice);
   }
   // Warm-start interpolation: Lagrange weights of the 17 nodes tau_{i N/16}
-  // (Chebyshev-Lobatto nodes of degree 16) at every node, in long double;
-  // rows of the 17 nodes themselves are exact unit vectors.
+  // (Chebyshev-Lobatto nodes of degree 16) at every node, in long double,
+  // stored as FP32 pairs hi + lo (L[j][i] then the remainders at offset
+  // n x 17); rows of the 17 nodes themselves are exact unit vectors.
   if (N % 16 == 0 && N >= 32) {
     p->kep_stride = N / 16;
-    std::vector<double> L((size_t)n * kKepNodes, 0.0);
+    std::vector<float> L(2 * (size_t)n * kKepNodes, 0.0f);
     for (int j = 0; j < n; j++) {
       if (j % p->kep_stride == 0) {
-        L[(size_t)j * kKepNodes + j / p->kep_stride] = 1.0;
+        L[(size_t)j * kKepNodes + j / p->kep_stride] = 1.0f;
         continue;
       }
       const long double x = (long double)p->h_tau[j];
@@ -184,11 +185,13 @@ extern "C" pc_status pc_plan_create(int N, int segments, const pc_force_model *f
         long double l = 1.0L;
         for (int k = 0; k < kKepNodes; k++)
           if (k != i) l *= (x - (long double)p->h_tau[k * p->kep_stride]) / (xi - (long double)p->h_tau[k * p->kep_stride]);
-        L[(size_t)j * kKepNodes + i] = (double)l;
+        const float hi = (float)l;
+        L[(size_t)j * kKepNodes + i] = hi;
+        L[((size_t)n + j) * kKepNodes + i] = (float)(l - (long double)hi);
       }
     }
     if (e == cudaSuccess) e = dalloc(&p->d_Lint, L.size());
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_Lint, L.data(), sizeof(double) * L.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_Lint, L.data(), sizeof(float) * L.size(), cudaMemcpyHostToDevice);
   }
   // Split-digit contraction: each operator row (node r+1) cut into 7 digits
   // against its largest exponent, packed as bf16 mma B fragments (B[k][n] =
@@ -346,7 +349,19 @@ pc_status pcx::ensure_workspace(pc_plan *p, long long n_ic, int mixed) {
     if (e == cudaSuccess) e = dalloc(&w.X32, n * (size_t)x32_stride((int)B) * ld);
     for (int b = 0; b < 2 && e == cudaSuccess; b++) e = dalloc(&w.R32[b], n * 6 * ld);
   }
-  if (p->kep_stride > 0 && e == cudaSuccess) e = dalloc(&w.YK17, (size_t)kKepNodes * 6 * ld);
+  if (p->kep_stride > 0 && e == cudaSuccess) e = dalloc(&w.YK17, 2 * (size_t)kKepNodes * 6 * ld);
+  if (B > 0 && e == cudaSuccess) {
+    // ephemeris cache: a table of at least twice the list capacity, and room
+    // for up to 32768 distinct node-time grids per round
+    long long sz = 1024;
+    while (sz < 2 * ld) sz *= 2;
+    w.eh_size = (int)sz;
+    w.eh_cap = (int)std::min<long long>(ld, 32768);
+    e = dalloc(&w.eh_tab, 4 * (size_t)sz);
+    if (e == cudaSuccess) e = dalloc(&w.eh_ent, (size_t)ld);
+    if (e == cudaSuccess) e = dalloc(&w.eh_own, (size_t)w.eh_cap);
+    if (e == cudaSuccess) e = dalloc(&w.EC, n * (3 * B + 3) * (size_t)w.eh_cap);
+  }
   if (e == cudaSuccess) e = dalloc(&w.lists, 6 * ld);
   if (e == cudaSuccess) e = dalloc(&w.pos, ld);
   if (e == cudaSuccess) e = dalloc(&w.cnt64, 2);
@@ -378,6 +393,10 @@ void pcx::free_workspace(pc_plan *p) {
   }
   cudaFree(w.YK);
   cudaFree(w.YK17);
+  cudaFree(w.eh_tab);
+  cudaFree(w.eh_ent);
+  cudaFree(w.eh_own);
+  cudaFree(w.EC);
   cudaFree(w.X32);
   for (int b = 0; b < 2; b++) cudaFree(w.R32[b]);
   cudaFree(w.G);

@@ -266,9 +266,10 @@ __device__ __forceinline__ bool kepler_interpolated(const Sweep &s, const Ctl &c
 
 // Warm start of the new segments at the 17 interpolation nodes j = i *
 // kep_stride (grid-stride over list entries x those nodes, entries fastest):
-// Kepler's equation solved as at every node before, NaN where the iteration
-// does not settle (k_setup then starts the whole segment cold).  Node 0 is the
-// start state itself.
+// Kepler's equation solved as at every node before, stored as the deviation
+// from the start state in an FP32 pair hi + lo (about 48 bits), NaN where the
+// iteration does not settle (k_setup then starts the whole segment cold).
+// Node 0 is the start state.
 __global__ void k_kepler17(Sweep s, Ctl c, const double *__restrict__ tau) {
   const int cur = s.list_cur;
   const long long count = s.list_cnt[cur];
@@ -293,8 +294,107 @@ __global__ void k_kepler17(Sweep s, Ctl c, const double *__restrict__ tau) {
     } else {
       for (int q = 0; q < 6; q++) y[q] = x0[q];
     }
-    for (int q = 0; q < 6; q++)
-      s.YK17[((size_t)k * 6 + q) * ld + e] = ok ? y[q] : __longlong_as_double(0x7FF8000000000000LL);
+    for (int q = 0; q < 6; q++) {
+      const double d = y[q] - x0[q];
+      const float hi = ok ? (float)d : __int_as_float(0x7FC00000);
+      s.YK17[((size_t)k * 6 + q) * ld + e] = hi;
+      s.YK17[((size_t)(kKepNodes + k) * 6 + q) * ld + e] = ok ? (float)(d - (double)hi) : hi;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Ephemeris of the new segments by node-time grid.  Segments with the same
+// (w1, w2) have the same node times t_j = w1 + w2 tau_j bit for bit (uniform
+// schedules over a common arc start many segments together), so the body
+// positions and the summed indirect term are evaluated once per grid:
+// k_grid_keys gives every list entry its grid's table slot (the first entry of
+// a grid owns it and takes the next cache index u), k_grid_ephem evaluates the
+// cache EC at every (grid, node), and k_setup copies from it.  The arithmetic
+// per node is the same as k_setup's own, so the copies are bitwise equal.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long grid_hash(unsigned long long a, unsigned long long b) {
+  // the splitmix64 finaliser (Steele, Lea and Flood; constants by Vigna) of a mix of both keys
+  unsigned long long x = a ^ (b * 0x9E3779B97F4A7C15ULL);
+  x ^= x >> 30;
+  x *= 0xBF58476D1CE4E5B9ULL;
+  x ^= x >> 27;
+  x *= 0x94D049BB133111EBULL;
+  x ^= x >> 31;
+  return x;
+}
+
+// Inserts list entry e's grid (k1, k2) = bits of (w1, w2) by linear probing
+// from slot hk; returns the slot holding the grid.  At most eh_size probes:
+// the table holds at least twice the list capacity, so a free slot exists.
+__device__ int grid_insert(const Sweep &s, const Ctl &c, int cur, int e, long long k1, long long k2,
+                           unsigned long long hk) {
+  int *tab = s.eh_tab[cur];
+  const unsigned msk = (unsigned)s.eh_size - 1u;
+  unsigned h = (unsigned)hk & msk;
+  for (int it = 0; it < s.eh_size; it++) {
+    const int o = atomicCAS(tab + h, -1, e);
+    if (o == -1) {
+      const int u = atomicAdd(s.eh_cnt + cur, 1);
+      if (u < s.eh_cap) s.eh_own[u] = e;
+      s.eh_uid[cur][h] = u < s.eh_cap ? u : -1;
+      return (int)h;
+    }
+    const int mo = s.list[cur][o];
+    if (__double_as_longlong(c.w1[mo]) == k1 && __double_as_longlong(c.w2[mo]) == k2) return (int)h;
+    h = (h + 1u) & msk;
+  }
+  return -1;
+}
+
+// One thread per list entry, whole warps per loop trip; the lanes of a warp
+// with the same grid insert it once (their leader's slot is shared).
+__global__ void k_grid_keys(Sweep s, Ctl c) {
+  const int cur = s.list_cur;
+  const long long count = s.list_cnt[cur];
+  const int *__restrict__ list = s.list[cur];
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long wb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); wb < count; wb += stride) {
+    const long long e = wb + lane;
+    const bool act = e < count;
+    const unsigned am = __ballot_sync(0xFFFFFFFFu, act);
+    if (!act) continue;
+    const int m = list[e];
+    const long long k1 = __double_as_longlong(c.w1[m]), k2 = __double_as_longlong(c.w2[m]);
+    const unsigned long long hk = grid_hash((unsigned long long)k1, (unsigned long long)k2);
+    const unsigned grp = __match_any_sync(am, hk);
+    const int leader = __ffs(grp) - 1;
+    const long long l1 = __shfl_sync(am, k1, leader), l2 = __shfl_sync(am, k2, leader);
+    const bool same = l1 == k1 && l2 == k2;
+    int h = -1;
+    if (lane == leader || !same) h = grid_insert(s, c, cur, (int)e, k1, k2, hk);
+    const int hl = __shfl_sync(am, h, leader);
+    s.eh_ent[e] = (same && lane != leader) ? hl : h;
+  }
+}
+
+// Body positions and summed indirect term of every cached grid at every node
+// (grid-stride over grids x nodes, grids fastest).
+__global__ void k_grid_ephem(Sweep s, Ctl c, Model md, const double *__restrict__ tau) {
+  const int cur = s.list_cur;
+  const long long U = min(s.eh_cnt[cur], s.eh_cap);
+  const long long total = U * s.n;
+  const int B = md.B;
+  const size_t cap = (size_t)s.eh_cap;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / U);
+    const long long u = i - (long long)j * U;
+    const int m = s.list[cur][s.eh_own[u]];
+    const double t = dadd(c.w1[m], dmul(c.w2[m], tau[j]));
+    double *ec = s.EC + (size_t)j * (3 * B + 3) * cap + u;
+    double ind[3] = {0.0, 0.0, 0.0};
+    ephem_all(md, ephem_locate(md, t), [&](int b, const double r[3]) {
+      for (int ax = 0; ax < 3; ax++) ec[(size_t)(3 * b + ax) * cap] = r[ax];
+      if (md.indirect) add_indirect(md, b, r, ind);
+    });
+    for (int ax = 0; ax < 3; ax++) ec[(size_t)(3 * B + ax) * cap] = ind[ax];
   }
 }
 
@@ -323,7 +423,13 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     s.lc_cnt[cur ^ 1] = 0;
     s.fp32_ctr[0] = 0;  // this round's FP32 kernels run after this kernel
     s.fp32_ctr[1] = 0;
+    if (s.eh_size > 0) s.eh_cnt[cur ^ 1] = 0;
   }
+  // the next round's grid table (this round's grids are read below)
+  if (s.eh_size > 0)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < s.eh_size;
+         i += (long long)gridDim.x * blockDim.x)
+      s.eh_tab[cur ^ 1][i] = -1;
   const long long count = s.list_cnt[cur];
   const int *__restrict__ list = s.list[cur];
   const long long total = count * s.n;
@@ -339,22 +445,35 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     bool ok = false;
     if (j > 0 && s.warm) {
       if (kepler_interpolated(s, c, m)) {
-        // interpolated from the 17 solved nodes (exact at those nodes)
-        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        // The deviation from the start state interpolated from the 17 solved
+        // nodes in compensated FP32 arithmetic (each product split exactly
+        // by an FMA, each sum by Knuth's TwoSum, the remainders and the lo
+        // parts summed beside): about 1e-13 of the deviation, as the FP64
+        // sum was, at the cost of FP32 operations.  The FP32 phase relies on
+        // this accuracy: it treats the warm start as an exact Kepler arc.
+        float sh[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, sl[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         bool fin = true;
-        const double *Lj = s.Lint + (size_t)j * kKepNodes;
-        for (int k = 0; k < kKepNodes; k++) {
-          const double l = Lj[k];
+        const float *Lh = s.Lint + (size_t)j * kKepNodes;
+        const float *Ll = s.Lint + ((size_t)s.n + j) * kKepNodes;
+        for (int k = 1; k < kKepNodes; k++) {
+          const float lh = Lh[k], ll = Ll[k];
 #pragma unroll
           for (int q = 0; q < 6; q++) {
-            const double v = s.YK17[((size_t)k * 6 + q) * ld + e];
-            fin = fin && isfinite(v);
-            acc[q] = fma(l, v, acc[q]);
+            const float dh = s.YK17[((size_t)k * 6 + q) * ld + e];
+            const float dl = s.YK17[((size_t)(kKepNodes + k) * 6 + q) * ld + e];
+            fin = fin && isfinite(dh);
+            const float pr = __fmul_rn(lh, dh);
+            const float pe = __fmaf_rn(lh, dh, -pr);  // lh dh - pr, exactly
+            const float sm = __fadd_rn(sh[q], pr);
+            const float bv = __fsub_rn(sm, sh[q]);
+            const float se = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(sm, bv)), __fsub_rn(pr, bv));  // sh + pr - sm
+            sh[q] = sm;
+            sl[q] = __fadd_rn(sl[q], __fadd_rn(__fadd_rn(se, pe), __fmaf_rn(lh, dl, __fmul_rn(ll, dh))));
           }
         }
         ok = fin;
         if (ok)
-          for (int q = 0; q < 6; q++) y[q] = acc[q];
+          for (int q = 0; q < 6; q++) y[q] = x0[q] + ((double)sh[q] + (double)sl[q]);
       } else {
         double kc[kKepConsts];
         for (int q = 0; q < kKepConsts; q++) kc[q] = c.kc[q * ld + m];
@@ -364,16 +483,31 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     if (!ok)
       for (int q = 0; q < 6; q++) y[q] = x0[q];
     float *rec = s.mixed ? mx.X32 + ((size_t)e * s.n + j) * mx.xs : nullptr;
-    const EphemLoc L = ephem_locate(md, t);
-    double ind[3] = {0.0, 0.0, 0.0};
-    ephem_all(md, L, [&](int b, const double r[3]) {
+    auto body = [&](int b, const double r[3]) {
       for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
-      if (md.indirect) add_indirect(md, b, r, ind);
       if (rec) {
         for (int ax = 0; ax < 3; ax++) rec[12 + 4 * b + ax] = (float)(y[ax] - r[ax]);
         rec[15 + 4 * b] = 0.0f;
       }
-    });
+    };
+    double ind[3] = {0.0, 0.0, 0.0};
+    const int slot = s.eh_size > 0 ? s.eh_ent[e] : -1;
+    const int u = slot >= 0 ? s.eh_uid[cur][slot] : -1;
+    if (u >= 0) {
+      // the segment's grid is cached
+      const size_t cap = (size_t)s.eh_cap;
+      const double *ec = s.EC + (size_t)j * (3 * B + 3) * cap + u;
+      for (int b = 0; b < B; b++) {
+        const double r[3] = {ec[(size_t)(3 * b) * cap], ec[(size_t)(3 * b + 1) * cap], ec[(size_t)(3 * b + 2) * cap]};
+        body(b, r);
+      }
+      for (int ax = 0; ax < 3; ax++) ind[ax] = ec[(size_t)(3 * B + ax) * cap];
+    } else {
+      ephem_all(md, ephem_locate(md, t), [&](int b, const double r[3]) {
+        if (md.indirect) add_indirect(md, b, r, ind);
+        body(b, r);
+      });
+    }
     for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
     if (rec) {
       double *yk = mx.YK + ((size_t)e * s.n + j) * 6;
@@ -1837,6 +1971,7 @@ cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cuda
   const Workspace &w = p->ws;
   cudaError_t e = cudaMemsetAsync(w.ints, 0, 16 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.cnt64, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && s.eh_size > 0) e = cudaMemsetAsync(s.eh_tab[0], 0xFF, 2 * sizeof(int) * s.eh_size, st);
   if (e != cudaSuccess) return e;
   p->acc_launches += 1;
   k_init<<<blocks_for(s.n_ic, kThreads), kThreads, 0, st>>>(s, w.ctl[w.live], p->model, x0, w.ints);
@@ -1863,6 +1998,11 @@ cudaError_t launch_round(const pc_plan *p, const Sweep &s, int cur, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[0], st);
+  if (s.eh_size > 0) {
+    k_grid_keys<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c);
+    k_grid_ephem<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->model, p->d_tau);
+    p->acc_launches += 2;
+  }
   if (s.warm && s.kep_stride > 0) {
     k_kepler17<<<sm_ctas(p, p->tune.setup_ctas_per_sm), kThreads, 0, sb>>>(s, c, p->d_tau);
     p->acc_launches += 1;

@@ -55,7 +55,8 @@ class KernelTimes(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("setup_ctas_per_sm", C.c_int), ("fp32_ctas_per_sm", C.c_int), ("contract_ctas_per_sm", C.c_int),
                 ("rounds_per_batch", C.c_int), ("repack_div", C.c_int), ("graphs", C.c_int),
-                ("side_priority", C.c_int), ("fp32_rows", C.c_int), ("fp32_slots", C.c_int)]
+                ("side_priority", C.c_int), ("fp32_rows", C.c_int), ("fp32_slots", C.c_int),
+                ("grid_cache", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

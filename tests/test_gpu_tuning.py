@@ -9,7 +9,7 @@ from paper_2301_03989_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 DEFAULT_TUNING = dict(setup_ctas_per_sm=4, fp32_ctas_per_sm=1, contract_ctas_per_sm=4, rounds_per_batch=8,
-                      repack_div=8, graphs=1, side_priority=1, fp32_rows=8, fp32_slots=16)
+                      repack_div=8, graphs=1, side_priority=1, fp32_rows=8, fp32_slots=16, grid_cache=1)
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +46,7 @@ def test_tunings_and_graphs_are_bitwise_neutral(pc, precision):
     settings = [dict(graphs=0), dict(graphs=1, rounds_per_batch=2), dict(contract_ctas_per_sm=1, setup_ctas_per_sm=1),
                 dict(contract_ctas_per_sm=8, fp32_ctas_per_sm=16, setup_ctas_per_sm=16),
                 dict(repack_div=2, rounds_per_batch=16), dict(repack_div=64, rounds_per_batch=5, graphs=1),
-                dict(side_priority=0, contract_ctas_per_sm=16),
+                dict(side_priority=0, contract_ctas_per_sm=16), dict(grid_cache=0),
                 # FP32 kernels: one trajectory per CTA, and tiles of 4 / 8 rows per thread with 8..64 slots
                 dict(fp32_rows=0, fp32_ctas_per_sm=4), dict(fp32_rows=4, fp32_slots=8, fp32_ctas_per_sm=2),
                 dict(fp32_rows=8, fp32_slots=32), dict(fp32_rows=4, fp32_slots=64, fp32_ctas_per_sm=3)]
@@ -88,12 +88,54 @@ def test_fp32_variants_are_bitwise_neutral_on_few_bodies(pc):
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grid_cache_is_bitwise_neutral_on_shared_grids(pc, precision):
+    """Config 3 (uniform segments over a common arc): most segments of a round
+    share their node times, so the set-up kernel copies body positions from the
+    per-grid ephemeris cache; with the cache off every segment evaluates its
+    own.  Both give bitwise the same results, order 1 and 2, and so does a
+    batch whose trajectories start at two different epochs."""
+    import torch
+    w = W.config3(M=1000)
+    prec = pc.PC_PREC_MIXED if precision == "mixed" else pc.PC_PREC_FP64
+    x0d = torch.as_tensor(W.to_planar(w.x0), device="cuda")
+    for order in (1, 2):
+        plan = pc.plan_from_workload(w, precision=prec, switch_tol=1e-6 if precision == "mixed" else 0.0,
+                                     order=order)
+        tf = 0.4 * W.YEAR
+        base = _run(pc, plan, w, x0d, tf)
+        assert base[0] == pc.PC_OK
+        pc.set_tuning(plan, grid_cache=0)
+        r = _run(pc, plan, w, x0d, tf)
+        for a, b in zip(base[2:], r[2:]):
+            assert torch.equal(a, b), order
+        plan.close()
+    # per-trajectory arcs from two epochs: two families of grids in one round
+    plan = pc.plan_from_workload(w, precision=prec, switch_tol=1e-6 if precision == "mixed" else 0.0)
+    M = 1000
+    t0 = torch.full((M,), w.t0, dtype=torch.float64, device="cuda")
+    t0[1::2] += 3.0 * W.DAY
+    tf = t0 + 0.3 * W.YEAR
+    outs = []
+    for gc in (1, 0):
+        pc.set_tuning(plan, grid_cache=gc)
+        xf = torch.zeros_like(x0d)
+        st = torch.zeros(M, dtype=torch.int32, device="cuda")
+        code, _ = pc.propagate_groups([plan], [M], x0d, t0, tf, xf, status=st)
+        torch.cuda.synchronize()
+        assert code == pc.PC_OK
+        outs.append(xf.clone())
+    assert torch.equal(outs[0], outs[1])
+    plan.close()
+
+
 def test_tuning_validation(pc):
     w = W.config1(M=8)
     plan = pc.plan_from_workload(w)
     for bad in (dict(setup_ctas_per_sm=0), dict(contract_ctas_per_sm=17), dict(rounds_per_batch=0),
                 dict(repack_div=1), dict(graphs=2), dict(fp32_ctas_per_sm=17), dict(side_priority=2),
-                dict(fp32_rows=2), dict(fp32_slots=12), dict(fp32_slots=0), dict(fp32_slots=72)):
+                dict(fp32_rows=2), dict(fp32_slots=12), dict(fp32_slots=0), dict(fp32_slots=72),
+                dict(grid_cache=2), dict(grid_cache=-1)):
         with pytest.raises(pc.PCError):
             pc.set_tuning(plan, **bad)
     assert pc.get_tuning(plan) == DEFAULT_TUNING
