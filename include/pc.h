@@ -280,12 +280,15 @@ pc_status pc_plan_kernel_times(pc_plan *plan, pc_kernel_times *out);
  *   fp32_rows             FP32 kernels: output rows per thread of the tiled
  *                         kernel (4 or 8), or 0 for one trajectory per CTA
  *   fp32_slots            FP32 kernels: trajectories per CTA of the tiled kernel
- *                         (8..64, a multiple of 8; fewer when N is large)
+ *                         (8..64, a multiple of 8; fewer when N is large or
+ *                         shared memory is short).  The slots' node records are
+ *                         staged in shared memory when they fit, else read from
+ *                         global memory (then up to 512 threads per CTA)
  *   grid_cache            1: the body positions at the nodes of a round's new
  *                         segments are evaluated once per distinct node-time grid
  *                         (segments with the same start and length share one) and
  *                         copied; 0: evaluated for every segment
- * Defaults: 4, 1, 4, 8, 8, 1, 1, 8, 16, 1.  Profiling (pc_plan_set_profiling)
+ * Defaults: 4, 1, 4, 8, 8, 1, 1, 4, 16, 1.  Profiling (pc_plan_set_profiling)
  * launches directly whatever `graphs` says. */
 typedef struct {
   int setup_ctas_per_sm;

@@ -226,7 +226,7 @@ struct pc_plan {
   int N = 0, n = 0, kpad = 0, rows_pad = 0;
   int segments = 0;
   pc_options opt{};
-  pc_tuning tune{4, 1, 4, 8, 8, 1, 1, 8, 16, 1};
+  pc_tuning tune{4, 1, 4, 8, 8, 1, 1, 4, 16, 1};
   long long session_id = 0;  // distinguishes calls for the graph cache
   int device = 0;
   // model (device copies)

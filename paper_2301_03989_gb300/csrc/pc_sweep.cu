@@ -1097,7 +1097,11 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
 // decision is made by thread t after the change and size maxima of the
 // slot's rows are reduced.
 // ---------------------------------------------------------------------------
-constexpr int kFp32tMaxThreads = 256;
+constexpr int kFp32tMaxThreads = 256;   // node records staged in shared memory
+constexpr int kFp32tMaxThreadsG = 512;  // node records read from global memory (4 rows per thread)
+__host__ __device__ constexpr int fp32t_max_threads(int R, bool rsm) {
+  return rsm ? kFp32tMaxThreads : (R == 4 ? kFp32tMaxThreadsG : kFp32tMaxThreads);
+}
 constexpr int kFp32tMaxSlots = 64;
 
 struct Fp32Slots {
@@ -1203,9 +1207,9 @@ __global__ void k_corr_setup(Sweep s, Model md, const float *__restrict__ mu32, 
 
 // Shared-memory bytes of the tiled FP32 kernel: operator (when staged), force
 // table, node records of the slots, reduction partials, GMs.
-__host__ __device__ inline size_t fp32t_smem_bytes(int n, int rows32, int T, int RG, bool ksm, int B) {
+__host__ __device__ inline size_t fp32t_smem_bytes(int n, int rows32, int T, int RG, bool ksm, bool rsm, int B) {
   const int xss = fp32_rec_stride(x32_stride(B));
-  return sizeof(float) * ((ksm ? (size_t)n * rows32 : 0) + (size_t)n * 6 * T + (size_t)T * n * xss +
+  return sizeof(float) * ((ksm ? (size_t)n * rows32 : 0) + (size_t)n * 6 * T + (rsm ? (size_t)T * n * xss : 0) +
                           2 * (size_t)T * (RG / 4) + B + 4);
 }
 
@@ -1216,8 +1220,8 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
-template <int MODE, int R, bool KSM>
-__global__ void __launch_bounds__(kFp32tMaxThreads, 1)
+template <int MODE, int R, bool KSM, bool RSM>
+__global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
     k_fp32t(Sweep s, Ctl c, Model md, const float *__restrict__ K32R, int rows32, const float *__restrict__ mu32,
             const double *__restrict__ Yc, double *__restrict__ Yn, const double *__restrict__ E,
             const float *__restrict__ R32, Mix mx, int T) {
@@ -1230,8 +1234,9 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
   float *Ks = reinterpret_cast<float *>(fp32t_sm4);          // [n][rows32] when KSM
   float *Gs = Ks + (KSM ? (size_t)n * rows32 : 0);             // [n][T][6]
   const int xs4 = mx.xs / 4, xss = fp32_rec_stride(mx.xs), xss4 = xss / 4;
-  float *Rs = Gs + (size_t)n * 6 * T;                          // [T][n][xss] node records of the slots
-  float *red = Rs + (size_t)T * n * xss;                       // [2][T][RG4]
+  float *Rs = Gs + (size_t)n * 6 * T;                          // [T][n][xss] node records of the slots (RSM)
+  float *red = Rs + (RSM ? (size_t)T * n * xss : 0);           // [2][T][RG4]
+  const int rstr = RSM ? xss4 : xs4;                           // float4s between the node records
   float *mus = red + 2 * T * RG4;                              // [B]
   const int cur = s.list_cur;
   const int count = MODE == FP32_KEPLER ? s.list_cnt[cur] : s.lc_cnt[cur];
@@ -1274,7 +1279,7 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       cp_async16(dst + (size_t)j * xss4 + v, src + idx);
     }
   };
-  if (e >= 0) load_records(e);
+  if (RSM && e >= 0) load_records(e);
   cp_async_wait_all();
   __syncthreads();
   float dl[R][6], acc[R][6];
@@ -1288,7 +1293,8 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
     }
     fresh = false;
     // force rows of the thread's nodes
-    const float4 *rb = reinterpret_cast<const float4 *>(Rs) + (size_t)t * n * xss4;
+    const float4 *rb = RSM ? reinterpret_cast<const float4 *>(Rs) + (size_t)t * n * xss4
+                           : reinterpret_cast<const float4 *>(mx.X32) + (size_t)(e >= 0 ? e : 0) * n * xs4;
     if (live) {
       float g[6];
       if (rg == 0) {
@@ -1303,7 +1309,7 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       for (int i = 0; i < R; i++) {
         const int j = j0 + i;
         if (j <= N) {
-          fp32_force_row<MODE>(rb + (size_t)j * xss4, B, mus, md.indirect, dl[i], w2f, g);
+          fp32_force_row<MODE>(rb + (size_t)j * rstr, B, mus, md.indirect, dl[i], w2f, g);
           float2 *gp = reinterpret_cast<float2 *>(Gs + ((size_t)j * T + t) * 6);
           gp[0] = make_float2(g[0], g[1]);
           gp[1] = make_float2(g[2], g[3]);
@@ -1383,7 +1389,7 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       for (int i = 0; i < R; i++) {
         const int j = j0 + i;
         if (j <= N) {
-          const float4 *rj = rb + (size_t)j * xss4;
+          const float4 *rj = rb + (size_t)j * rstr;
           const float4 rk = rj[0], vk = rj[1];
           const float yk[6] = {rk.x, rk.y, rk.z, vk.x, vk.y, vk.z};
           float res[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -1513,7 +1519,7 @@ __global__ void __launch_bounds__(kFp32tMaxThreads, 1)
       m = sl.m[t];
       w2f = sl.w2[t];
       fresh = true;
-      if (e >= 0) load_records(e);
+      if (RSM && e >= 0) load_records(e);
     }
     cp_async_wait_all();
     __syncthreads();  // the new trajectories' records are in place
@@ -1863,54 +1869,96 @@ size_t fp32_smem_bytes(const pc_plan *p) {
   return sizeof(float) * ((size_t)p->n * (xss + 6) + 2 * (threads / 32));
 }
 
-// Launch shape of the tiled FP32 kernel under the plan's tuning: R rows per
-// thread, RG = 4 ceil(N / 4R) row groups, T slots (a multiple of 8, at most
-// 256 / RG threads' worth and as many as fit in shared memory with their
-// node records), the operator staged in shared memory when it fits.  ok = 0
-// when even 8 slots exceed 256 threads (N > 256) or shared memory: one
-// trajectory per CTA then.
+// Launch shape of the tiled FP32 kernel: R rows per thread, RG row groups
+// (threads per slot), T trajectory slots per CTA.  Node records either staged
+// in shared memory (at most 256 threads) or read from global memory through
+// L1 (4 rows per thread: up to 512 threads, 16 warps, in the shared memory
+// the records would take); the operator in shared memory, or read through L1
+// when it does not fit beside staged records.  The slot count asked for is
+// met with staged records when they fit, else by reading them from global
+// memory; failing both (N > 256) one trajectory per CTA.
 struct Fp32tShape {
   int R, RG, T, threads;
-  bool ksm, ok;
+  bool ksm, rsm, ok;
   size_t smem;
 };
 constexpr size_t kMaxDynSmem = 220 * 1024;
 
 Fp32tShape fp32t_shape(const pc_plan *p) {
   Fp32tShape sh{};
-  const int N = p->N;
+  const int N = p->N, n = p->n, B = p->model.B;
   sh.R = p->tune.fp32_rows == 4 ? 4 : 8;
   sh.RG = 4 * ((N + 4 * sh.R - 1) / (4 * sh.R));
-  if (sh.R == 4 && sh.RG * 8 > kFp32tMaxThreads) {
+  if (sh.R == 4 && sh.RG * 8 > kFp32tMaxThreadsG) {
     sh.R = 8;
     sh.RG = 4 * ((N + 31) / 32);
   }
-  sh.ok = p->tune.fp32_rows != 0 && sh.RG * 8 <= kFp32tMaxThreads;
-  const int tmax = std::min(kFp32tMaxSlots, std::max(8, kFp32tMaxThreads / sh.RG / 8 * 8));
-  sh.T = std::max(8, std::min(p->tune.fp32_slots / 8 * 8, tmax));
-  // the largest slot count whose node records fit beside the staged operator;
-  // failing that 8 slots with the operator read through L1; failing that
-  // (many bodies) one trajectory per CTA
-  const int B = p->model.B;
-  while (sh.T > 8 && fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, true, B) > kMaxDynSmem) sh.T -= 8;
-  sh.ksm = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, true, B) <= kMaxDynSmem;
-  if (!sh.ksm && fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, false, B) > kMaxDynSmem) sh.ok = false;
+  sh.ok = false;
+  if (p->tune.fp32_rows == 0 || sh.RG * 8 > kFp32tMaxThreads) return sh;
+  const int want = std::max(8, std::min(p->tune.fp32_slots / 8 * 8, kFp32tMaxSlots));
+  // largest T <= want (multiple of 8) for a variant, 0 if none
+  auto slots = [&](bool ksm, bool rsm) {
+    int T = std::min(want, fp32t_max_threads(sh.R, rsm) / sh.RG / 8 * 8);
+    while (T >= 8 && fp32t_smem_bytes(n, p->rows32, T, sh.RG, ksm, rsm, B) > kMaxDynSmem) T -= 8;
+    return T >= 8 ? T : 0;
+  };
+  const int t_staged = slots(true, true);
+  const int t_global = slots(true, false);
+  if (t_staged > 0 && t_staged >= t_global) {
+    sh.T = t_staged;
+    sh.ksm = sh.rsm = true;
+  } else if (t_global > 0) {
+    sh.T = t_global;
+    sh.ksm = true;
+    sh.rsm = false;
+  } else if (slots(false, true) > 0) {
+    sh.T = slots(false, true);
+    sh.ksm = false;
+    sh.rsm = true;
+  } else {
+    return sh;
+  }
+  sh.ok = true;
   sh.threads = sh.RG * sh.T;
-  sh.smem = fp32t_smem_bytes(p->n, p->rows32, sh.T, sh.RG, sh.ksm, B);
+  sh.smem = fp32t_smem_bytes(n, p->rows32, sh.T, sh.RG, sh.ksm, sh.rsm, B);
   return sh;
 }
 
-template <int MODE, int R, bool KSM>
+template <int MODE, int R, bool KSM, bool RSM>
 void launch_fp32t_one(const pc_plan *p, const Fp32tShape &sh, const Sweep &s, const double *Yc, double *Yn,
                       const double *E, const float *R32, const Mix &mx, cudaStream_t st) {
   const Ctl &c = p->ws.ctl[p->ws.live];
-  k_fp32t<MODE, R, KSM><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), sh.threads, sh.smem, st>>>(
+  k_fp32t<MODE, R, KSM, RSM><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), sh.threads, sh.smem, st>>>(
       s, c, p->model, p->d_K32R, p->rows32, p->d_mu32, Yc, Yn, E, R32, mx, sh.T);
 }
 
-template <int MODE, int R, bool KSM>
+template <int MODE, int R, bool KSM, bool RSM>
 cudaError_t fp32t_attr(size_t smem) {
-  return cudaFuncSetAttribute(k_fp32t<MODE, R, KSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_fp32t<MODE, R, KSM, RSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int MODE, int R>
+void launch_fp32t_r(const pc_plan *p, const Fp32tShape &sh, const Sweep &s, const double *Yc, double *Yn,
+                    const double *E, const float *R32, const Mix &mx, cudaStream_t st) {
+  if (!sh.rsm) launch_fp32t_one<MODE, R, true, false>(p, sh, s, Yc, Yn, E, R32, mx, st);
+  else if (sh.ksm) launch_fp32t_one<MODE, R, true, true>(p, sh, s, Yc, Yn, E, R32, mx, st);
+  else launch_fp32t_one<MODE, R, false, true>(p, sh, s, Yc, Yn, E, R32, mx, st);
+}
+
+template <int R>
+cudaError_t fp32t_attr_r(const Fp32tShape &sh) {
+  cudaError_t e;
+  if (!sh.rsm) {
+    e = fp32t_attr<FP32_KEPLER, R, true, false>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, R, true, false>(sh.smem);
+  } else if (sh.ksm) {
+    e = fp32t_attr<FP32_KEPLER, R, true, true>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, R, true, true>(sh.smem);
+  } else {
+    e = fp32t_attr<FP32_KEPLER, R, false, true>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, R, false, true>(sh.smem);
+  }
+  return e;
 }
 
 // FP32 sweeps of one mode over this round's list: the tiled kernel (T
@@ -1928,13 +1976,8 @@ void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn,
                                                                              Yc, Yn, E, R32, mx);
     return;
   }
-  if (sh.R == 4) {
-    if (sh.ksm) launch_fp32t_one<MODE, 4, true>(p, sh, s, Yc, Yn, E, R32, mx, st);
-    else launch_fp32t_one<MODE, 4, false>(p, sh, s, Yc, Yn, E, R32, mx, st);
-  } else {
-    if (sh.ksm) launch_fp32t_one<MODE, 8, true>(p, sh, s, Yc, Yn, E, R32, mx, st);
-    else launch_fp32t_one<MODE, 8, false>(p, sh, s, Yc, Yn, E, R32, mx, st);
-  }
+  if (sh.R == 4) launch_fp32t_r<MODE, 4>(p, sh, s, Yc, Yn, E, R32, mx, st);
+  else launch_fp32t_r<MODE, 8>(p, sh, s, Yc, Yn, E, R32, mx, st);
 }
 
 }  // namespace
@@ -1951,20 +1994,7 @@ cudaError_t prepare_launches(const pc_plan *p) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fp32<FP32_CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   const Fp32tShape sh = fp32t_shape(p);
   if (e != cudaSuccess || !sh.ok) return e;
-  if (sh.R == 4 && sh.ksm) {
-    e = fp32t_attr<FP32_KEPLER, 4, true>(sh.smem);
-    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 4, true>(sh.smem);
-  } else if (sh.R == 4) {
-    e = fp32t_attr<FP32_KEPLER, 4, false>(sh.smem);
-    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 4, false>(sh.smem);
-  } else if (sh.ksm) {
-    e = fp32t_attr<FP32_KEPLER, 8, true>(sh.smem);
-    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 8, true>(sh.smem);
-  } else {
-    e = fp32t_attr<FP32_KEPLER, 8, false>(sh.smem);
-    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 8, false>(sh.smem);
-  }
-  return e;
+  return sh.R == 4 ? fp32t_attr_r<4>(sh) : fp32t_attr_r<8>(sh);
 }
 
 cudaError_t launch_init(const pc_plan *p, const Sweep &s, const double *x0, cudaStream_t st) {

@@ -9,7 +9,7 @@ from paper_2301_03989_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 DEFAULT_TUNING = dict(setup_ctas_per_sm=4, fp32_ctas_per_sm=1, contract_ctas_per_sm=4, rounds_per_batch=8,
-                      repack_div=8, graphs=1, side_priority=1, fp32_rows=8, fp32_slots=16, grid_cache=1)
+                      repack_div=8, graphs=1, side_priority=1, fp32_rows=4, fp32_slots=16, grid_cache=1)
 
 
 @pytest.fixture(scope="module")
@@ -78,8 +78,11 @@ def test_fp32_variants_are_bitwise_neutral_on_few_bodies(pc):
     pc.set_tuning(plan, fp32_rows=0, fp32_ctas_per_sm=4)
     base = _run(pc, plan, w, x0d, tf)
     assert base[0] == pc.PC_OK
+    # 8 slots stage their node records in shared memory; 16 and more read them
+    # from global memory (4 rows per thread: 512 threads per CTA)
     for kw in (dict(fp32_rows=4, fp32_slots=8, fp32_ctas_per_sm=1), dict(fp32_rows=8, fp32_slots=8),
-               dict(fp32_rows=4, fp32_slots=64, fp32_ctas_per_sm=2), dict(fp32_rows=8, fp32_slots=16, graphs=0)):
+               dict(fp32_rows=4, fp32_slots=16), dict(fp32_rows=4, fp32_slots=64, fp32_ctas_per_sm=2),
+               dict(fp32_rows=8, fp32_slots=16, graphs=0)):
         pc.set_tuning(plan, **kw)
         r = _run(pc, plan, w, x0d, tf)
         for a, b in zip(base[2:], r[2:]):
