@@ -89,30 +89,78 @@ __device__ void kepler_consts(double mu, const double x0[6], double c[kKepConsts
   c[10] = r0;
 }
 
+// The iteration runs first in FP32 (same steps and bracket, to a step below
+// 2e-6), which leaves the FP64 iteration one Halley step from that start in
+// the usual case; the sine and cosine at the root then follow from those at
+// the last iterate by the angle-addition formulas with the step's Taylor
+// series (|step| <= 1e-5: the dropped terms are below 1e-32).  Only when the
+// FP32 start is poor does the FP64 iteration take more steps.  An iterate
+// with F = 0 is the root, and a Halley step onto the bracket's end is kept:
+// at the root rounding can put the step exactly there, and bisecting from
+// it would cost some thirty steps.
 __device__ bool kepler_solve(const double c[kKepConsts], const double x0[6], double dt, double out[6]) {
   if (!(c[0] > 0.0)) return false;
   const double a = c[1], ecE = c[2], esE = c[3];
   const double M = c[4] * dt;
   double lo = M - 2.0, hi = M + 2.0;
   double X = fmin(fmax(M * c[6], lo + 0.5), hi - 0.5);
+  {
+    const float Mf = (float)M, ef = (float)ecE, sf = (float)esE;
+    float lof = (float)lo, hif = (float)hi, Xf = (float)X;
+    for (int it = 0; it < 32; it++) {
+      float sXf, cXf;
+      sincosf(Xf, &sXf, &cXf);
+      const float F = Xf - ef * sXf + sf * (1.0f - cXf) - Mf;
+      if (F == 0.0f) break;
+      if (F > 0.0f) hif = Xf; else lof = Xf;
+      const float d1 = 1.0f - ef * cXf + sf * sXf;
+      const float d2 = ef * sXf + sf * cXf;
+      float Xn = Xf - 2.0f * F * d1 / (2.0f * d1 * d1 - F * d2);
+      if (!(Xn >= lof && Xn <= hif)) Xn = 0.5f * (lof + hif);
+      const float step = fabsf(Xn - Xf);
+      Xf = Xn;
+      if (!(step > 2e-6f * (1.0f + fabsf(Xf)))) break;
+    }
+    if (isfinite(Xf)) X = fmin(fmax((double)Xf, lo), hi);
+  }
   bool ok = false;
+  double sX = 0.0, cX = 1.0, dl = 0.0;  // sine, cosine at the last evaluated iterate, step from it
+  bool rotate = false;
   for (int it = 0; it < 64; it++) {
-    double sX, cX;
     sincos(X, &sX, &cX);
     const double F = X - ecE * sX + esE * (1.0 - cX) - M;
+    if (F == 0.0) {
+      ok = rotate = true;  // dl = 0: sX, cX are the root's
+      dl = 0.0;
+      break;
+    }
     if (F > 0.0) hi = X; else lo = X;
     const double d1 = 1.0 - ecE * cX + esE * sX;
     const double d2 = ecE * sX + esE * cX;
     double Xn = X - 2.0 * F * d1 / (2.0 * d1 * d1 - F * d2);
-    const bool halley = Xn > lo && Xn < hi;
+    const bool halley = Xn >= lo && Xn <= hi;
     if (!halley) Xn = 0.5 * (lo + hi);
-    const double step = fabs(Xn - X);
+    dl = Xn - X;
+    const double step = fabs(dl);
     X = Xn;
-    if ((halley && step <= 1e-6 * (1.0 + fabs(X))) || step <= 1e-15 * (1.0 + fabs(X))) { ok = true; break; }
+    if ((halley && step <= 1e-6 * (1.0 + fabs(X))) || step <= 1e-15 * (1.0 + fabs(X))) {
+      ok = true;
+      rotate = step <= 1e-5;
+      break;
+    }
   }
   if (!ok) return false;
-  double sX, cX;
-  sincos(X, &sX, &cX);
+  if (rotate) {
+    // sin, cos at X = (previous iterate) + dl by angle addition
+    const double d2 = dl * dl;
+    const double sd = dl * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * 0.05));
+    const double cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0));
+    const double s1 = sX * cd + cX * sd, c1 = cX * cd - sX * sd;
+    sX = s1;
+    cX = c1;
+  } else {
+    sincos(X, &sX, &cX);
+  }
   const double omc = 1.0 - cX;
   const double r = a + (c[10] - a) * cX + c[5] * sX;
   const double f = 1.0 - c[6] * omc;
@@ -485,10 +533,9 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     float *rec = s.mixed ? mx.X32 + ((size_t)e * s.n + j) * mx.xs : nullptr;
     auto body = [&](int b, const double r[3]) {
       for (int ax = 0; ax < 3; ax++) E[((size_t)(j * B + b) * 3 + ax) * ld + m] = r[ax];
-      if (rec) {
-        for (int ax = 0; ax < 3; ax++) rec[12 + 4 * b + ax] = (float)(y[ax] - r[ax]);
-        rec[15 + 4 * b] = 0.0f;
-      }
+      if (rec)
+        reinterpret_cast<float4 *>(rec)[3 + b] =
+            make_float4((float)(y[0] - r[0]), (float)(y[1] - r[1]), (float)(y[2] - r[2]), 0.0f);
     };
     double ind[3] = {0.0, 0.0, 0.0};
     const int slot = s.eh_size > 0 ? s.eh_ent[e] : -1;
@@ -510,19 +557,16 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
     }
     for (int ax = 0; ax < 3; ax++) Aind[(size_t)(j * 3 + ax) * ld + m] = ind[ax];
     if (rec) {
-      double *yk = mx.YK + ((size_t)e * s.n + j) * 6;
-      for (int q = 0; q < 6; q++) yk[q] = y[q];
+      // 16-byte stores: a record is 12 + 4B floats, a warm start 6 doubles
+      double2 *yk = reinterpret_cast<double2 *>(mx.YK + ((size_t)e * s.n + j) * 6);
+      yk[0] = make_double2(y[0], y[1]);
+      yk[1] = make_double2(y[2], y[3]);
+      yk[2] = make_double2(y[4], y[5]);
       const double rr = rsqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
-      rec[0] = (float)y[0];
-      rec[1] = (float)y[1];
-      rec[2] = (float)y[2];
-      rec[3] = (float)(md.mu_c * rr * rr * rr);
-      rec[4] = (float)y[3];
-      rec[5] = (float)y[4];
-      rec[6] = (float)y[5];
-      rec[7] = 0.0f;
-      for (int ax = 0; ax < 3; ax++) rec[8 + ax] = (float)ind[ax];
-      rec[11] = 0.0f;
+      float4 *r4 = reinterpret_cast<float4 *>(rec);
+      r4[0] = make_float4((float)y[0], (float)y[1], (float)y[2], (float)(md.mu_c * rr * rr * rr));
+      r4[1] = make_float4((float)y[3], (float)y[4], (float)y[5], 0.0f);
+      r4[2] = make_float4((float)ind[0], (float)ind[1], (float)ind[2], 0.0f);
     } else {
       for (int q = 0; q < 6; q++) Y[(size_t)(j * 6 + q) * ld + m] = y[q];
     }
