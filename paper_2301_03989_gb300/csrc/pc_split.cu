@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
             for (int dd = 0; dd < kSplitDigits; dd++) S[dd] = (long long)__float2int_rn(acc[mt][dd][idx]);
             const long long vhi = S[0] * (1LL << 24) + S[1] * (1LL << 16) + S[2] * (1LL << 8) + S[3];
             const long long vlo = S[4] * (1LL << 16) + S[5] * (1LL << 8) + S[6];
-            const double v = fma((double)vlo, 0x1p-24, (double)vhi) * pow2i(kx + colB[row] - 2042 - 40);
-            yq[q] = c.x[(size_t)(Q0 + q) * ld + m] + v;
+            // x0 + v 2^e in one rounding (the power-of-two scaling is exact)
+            yq[q] = fma(fma((double)vlo, 0x1p-24, (double)vhi), pow2i(kx + colB[row] - 2042 - 40),
+                        c.x[(size_t)(Q0 + q) * ld + m]);
           }
           if (bad[tt])
 #pragma unroll
@@ -224,23 +225,30 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
             double yn[6];
 #pragma unroll
             for (int q = 0; q < 6; q++) yn[q] = (q < NC) ? yq[q] : Ynew[base + (size_t)q * ld];
-            double d[6];
+            // the sweep's change, rounded to FP32: the residual an FP32
+            // correction solve starts from next round, and (scaled by the
+            // new iterate's |r| and |v|) the convergence measure, whose
+            // decisions need a few digits, not FP64 -- GB300's FP64 pipe is
+            // this epilogue's bound
+            float df[6];
 #pragma unroll
-            for (int q = 0; q < 6; q++) d[q] = yn[q] - Yold[base + (size_t)q * ld];
-            if (R32)  // the sweep's residual, for an FP32 correction solve next round
+            for (int q = 0; q < 6; q++) df[q] = (float)(yn[q] - Yold[base + (size_t)q * ld]);
+            if (R32)
 #pragma unroll
-              for (int q = 0; q < 6; q++) R32[base + (size_t)q * ld] = (float)d[q];
+              for (int q = 0; q < 6; q++) R32[base + (size_t)q * ld] = df[q];
+            float sr = 1.0f, sv = 1.0f;
+            if (s.relative) {
+              const float nr = (float)fma(yn[2], yn[2], fma(yn[1], yn[1], yn[0] * yn[0]));
+              const float nv = (float)fma(yn[5], yn[5], fma(yn[4], yn[4], yn[3] * yn[3]));
+              sr = (nr > 0.0f && nr <= 3.0e38f) ? rsqrtf(nr) : 1.0f;
+              sv = (nv > 0.0f && nv <= 3.0e38f) ? rsqrtf(nv) : 1.0f;
+            }
             // squared change of |r| and |v| relative to the new iterate (one
             // square root per trajectory, after the maximum)
-            double dr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            double dv = d[3] * d[3] + d[4] * d[4] + d[5] * d[5];
-            if (s.relative) {
-              const double nr = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
-              const double nv = yn[3] * yn[3] + yn[4] * yn[4] + yn[5] * yn[5];
-              if (nr > 0.0) dr = dr / nr;
-              if (nv > 0.0) dv = dv / nv;
-            }
-            e2 = nanmax(e2, nanmax(dr, dv));
+            const float r0 = df[0] * sr, r1 = df[1] * sr, r2 = df[2] * sr;
+            const float v0 = df[3] * sv, v1 = df[4] * sv, v2 = df[5] * sv;
+            const float dr = r0 * r0 + r1 * r1 + r2 * r2, dv = v0 * v0 + v1 * v1 + v2 * v2;
+            e2 = nanmax(e2, (double)nanmaxf(dr, dv));
           }
         }
         if (EPI == EPI_FULL || EPI == EPI_POS) {
