@@ -88,6 +88,7 @@ extern "C" pc_status pc_options_default(pc_options *o) {
   o->refine32 = 1;
   o->contraction = PC_CONTRACT_SPLIT;
   o->order = 1;
+  o->fp32_mma = 1;
   return PC_OK;
 }
 
@@ -97,7 +98,7 @@ static pc_status check_options(const pc_options &o) {
       (o.precision != PC_PREC_FP64 && o.precision != PC_PREC_MIXED) || o.max_rounds < 0 ||
       !(o.switch_tol >= 0.0) || (o.refine32 != 0 && o.refine32 != 1) ||
       (o.contraction != PC_CONTRACT_DMMA && o.contraction != PC_CONTRACT_SPLIT) || (o.order != 1 && o.order != 2) ||
-      (o.order == 2 && o.contraction != PC_CONTRACT_SPLIT))
+      (o.order == 2 && o.contraction != PC_CONTRACT_SPLIT) || (o.fp32_mma != 0 && o.fp32_mma != 1))
     return PC_EINVAL;
   return PC_OK;
 }

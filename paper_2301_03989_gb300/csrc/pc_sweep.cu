@@ -1249,12 +1249,99 @@ __global__ void k_corr_setup(Sweep s, Model md, const float *__restrict__ mu32, 
   }
 }
 
-// Shared-memory bytes of the tiled FP32 kernel: operator (when staged), force
-// table, node records of the slots, reduction partials, GMs.
-__host__ __device__ inline size_t fp32t_smem_bytes(int n, int rows32, int T, int RG, bool ksm, bool rsm, int B) {
-  const int xss = fp32_rec_stride(x32_stride(B));
-  return sizeof(float) * ((ksm ? (size_t)n * rows32 : 0) + (size_t)n * 6 * T + (rsm ? (size_t)T * n * xss : 0) +
-                          2 * (size_t)T * (RG / 4) + B + 4);
+// Shared-memory layout of the tiled FP32 kernel (floats): operator (when
+// staged), force table, MMA output table (tensor-core contraction), node
+// records of the slots (when staged), reduction partials, GMs.  With the
+// tensor-core contraction the operator rows are 16 MT + 8 floats long and the
+// table rows 6T + 8 (k-rows padded to a multiple of 8 with zeros), so that
+// the fragment loads of a warp fall in 32 distinct banks.
+struct Fp32tLayout {
+  size_t ks, gs, os, rs;  // sizes of the four arrays
+  int kst, gst;           // row strides of the operator and the force table
+};
+__host__ __device__ inline Fp32tLayout fp32t_layout(int N, int n, int rows32, int T, bool ksm, bool rsm, bool mma,
+                                                    int B) {
+  Fp32tLayout L;
+  const int MT = (N + 15) / 16, kp8 = (n + 7) / 8 * 8;
+  L.kst = mma ? 16 * MT + 8 : rows32;
+  L.gst = 6 * T + (mma ? 8 : 0);
+  L.ks = ksm ? (size_t)(mma ? kp8 : n) * L.kst : 0;
+  L.gs = (size_t)(mma ? kp8 : n) * L.gst;
+  L.os = mma ? (size_t)16 * MT * L.gst : 0;
+  L.rs = rsm ? (size_t)T * n * fp32_rec_stride(x32_stride(B)) : 0;
+  return L;
+}
+__host__ __device__ inline size_t fp32t_smem_bytes(int N, int n, int rows32, int T, int RG, bool ksm, bool rsm,
+                                                   bool mma, int B) {
+  const Fp32tLayout L = fp32t_layout(N, n, rows32, T, ksm, rsm, mma, B);
+  return sizeof(float) * (L.ks + L.gs + L.os + L.rs + 2 * (size_t)T * (RG / 4) + B + 4);
+}
+
+// TF32 high part of x: x rounded to 10 mantissa bits (to nearest, ties away
+// from zero: half a TF32 ulp added to the bit pattern, the low 13 bits
+// cleared), as mma operand bits.  x - hi is exact in FP32, at most 2^-11 |x|
+// and of either sign; passed as an operand, the tensor core keeps its leading
+// 11 bits, so hi and lo together carry x to about 2^-22.  Integer operations
+// instead of conversions, which run at a fraction of the FP32 rate.
+__device__ __forceinline__ unsigned tf32_hi(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The operator contraction of one FP32 sweep (or pass) on the tensor cores:
+// O[r][c] = sum_k K[r+1][k] G[k][c] over the CTA's T slots, column c = (slot
+// c / NC, component Q0 + c % NC).  Each operand is split into TF32 high and
+// low parts and the product taken as K_lo G_hi + K_hi G_lo + K_hi G_hi (the
+// dropped K_lo G_lo is below 2^-22 of the term), accumulated in FP32: close
+// to the accuracy of FP32 multiply-adds.  The CTA's MT x (T/8) warps each take
+// one 16-row tile and NC column tiles of 8; A fragments come from the operator
+// (Ks[k][r]), B fragments from the force table, and the results go to Os.
+template <int NC, int Q0>
+__device__ __forceinline__ void fp32_mma_contract(const float *__restrict__ Ks, int kst, const float *__restrict__ Gs,
+                                                  int gst, float *__restrict__ Os, int MT, int kp8) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int mt = w % MT, part = w / MT;
+  float acc[NC][4];
+  int boff[NC];
+#pragma unroll
+  for (int jn = 0; jn < NC; jn++) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[jn][i] = 0.0f;
+    const int col = (part * NC + jn) * 8 + g;
+    boff[jn] = (col / NC) * 6 + Q0 + col % NC;
+  }
+  const float *A0 = Ks + mt * 16 + g;
+  for (int k0 = 0; k0 < kp8; k0 += 8) {
+    const float *Ak = A0 + (size_t)(k0 + t4) * kst;
+    const float av[4] = {Ak[0], Ak[8], Ak[(size_t)4 * kst], Ak[(size_t)4 * kst + 8]};
+    unsigned ah[4], al[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      ah[i] = tf32_hi(av[i]);
+      al[i] = __float_as_uint(av[i] - __uint_as_float(ah[i]));
+    }
+    const float *Bk = Gs + (size_t)(k0 + t4) * gst;
+#pragma unroll
+    for (int jn = 0; jn < NC; jn++) {
+      const float b0 = Bk[boff[jn]], b1 = Bk[(size_t)4 * gst + boff[jn]];
+      const unsigned bh0 = tf32_hi(b0), bh1 = tf32_hi(b1);
+      const unsigned bl0 = __float_as_uint(b0 - __uint_as_float(bh0)), bl1 = __float_as_uint(b1 - __uint_as_float(bh1));
+      mma_tf32_1688(acc[jn], al, bh0, bh1);
+      mma_tf32_1688(acc[jn], ah, bl0, bl1);
+      mma_tf32_1688(acc[jn], ah, bh0, bh1);
+    }
+  }
+#pragma unroll
+  for (int jn = 0; jn < NC; jn++) {
+    const int col = (part * NC + jn) * 8 + 2 * t4;
+    *reinterpret_cast<float2 *>(Os + (size_t)(mt * 16 + g) * gst + col) = make_float2(acc[jn][0], acc[jn][1]);
+    *reinterpret_cast<float2 *>(Os + (size_t)(mt * 16 + g + 8) * gst + col) = make_float2(acc[jn][2], acc[jn][3]);
+  }
 }
 
 // 16-byte asynchronous copy global -> shared (no register staging).
@@ -1264,7 +1351,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
-template <int MODE, int R, bool KSM, bool RSM>
+template <int MODE, int R, bool KSM, bool RSM, bool MMA>
 __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
     k_fp32t(Sweep s, Ctl c, Model md, const float *__restrict__ K32R, int rows32, const float *__restrict__ mu32,
             const double *__restrict__ Yc, double *__restrict__ Yn, const double *__restrict__ E,
@@ -1275,11 +1362,14 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
   const int RG = blockDim.x / T, RG4 = RG / 4;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int rg_hi = wid % RG4, rg = rg_hi * 4 + (lane & 3), t = (wid / RG4) * 8 + (lane >> 2);
-  float *Ks = reinterpret_cast<float *>(fp32t_sm4);          // [n][rows32] when KSM
-  float *Gs = Ks + (KSM ? (size_t)n * rows32 : 0);             // [n][T][6]
+  const Fp32tLayout lay = fp32t_layout(N, n, rows32, T, KSM, RSM, MMA, B);
+  const int gst = lay.gst, MT = (N + 15) / 16, kp8 = (n + 7) / 8 * 8;
+  float *Ks = reinterpret_cast<float *>(fp32t_sm4);          // [n or kp8][kst] when KSM
+  float *Gs = Ks + lay.ks;                                     // [n or kp8][gst]: slot t at t * 6
+  float *Os = Gs + lay.gs;                                     // [16 MT][gst] tensor-core results (MMA)
   const int xs4 = mx.xs / 4, xss = fp32_rec_stride(mx.xs), xss4 = xss / 4;
-  float *Rs = Gs + (size_t)n * 6 * T;                          // [T][n][xss] node records of the slots (RSM)
-  float *red = Rs + (RSM ? (size_t)T * n * xss : 0);           // [2][T][RG4]
+  float *Rs = Os + lay.os;                                     // [T][n][xss] node records of the slots (RSM)
+  float *red = Rs + lay.rs;                                    // [2][T][RG4]
   const int rstr = RSM ? xss4 : xs4;                           // float4s between the node records
   float *mus = red + 2 * T * RG4;                              // [B]
   const int cur = s.list_cur;
@@ -1289,9 +1379,17 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
   int *ctr = s.fp32_ctr + (MODE == FP32_KEPLER ? 0 : 1);
   const int first_refill = gridDim.x * T;
 
-  if (KSM)
+  if (MMA) {
+    // operator rows padded to kst, k-rows n..kp8-1 of both tables zero
+    for (int i = tid; i < kp8 * lay.kst; i += blockDim.x) {
+      const int k = i / lay.kst, r = i - k * lay.kst;
+      Ks[i] = (k < n && r < rows32) ? __ldg(K32R + (size_t)k * rows32 + r) : 0.0f;
+    }
+    for (int i = n * gst + tid; i < kp8 * gst; i += blockDim.x) Gs[i] = 0.0f;
+  } else if (KSM) {
     for (int i = tid; i < n * rows32 / 4; i += blockDim.x)
       reinterpret_cast<float4 *>(Ks)[i] = __ldg(reinterpret_cast<const float4 *>(K32R) + i);
+  }
   for (int b = tid; b < B; b += blockDim.x) mus[b] = mu32[b];
   if (tid < T) {
     const int e = tid * gridDim.x + blockIdx.x;
@@ -1354,7 +1452,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
         const int j = j0 + i;
         if (j <= N) {
           fp32_force_row<MODE>(rb + (size_t)j * rstr, B, mus, md.indirect, dl[i], w2f, g);
-          float2 *gp = reinterpret_cast<float2 *>(Gs + ((size_t)j * T + t) * 6);
+          float2 *gp = reinterpret_cast<float2 *>(Gs + (size_t)j * gst + t * 6);
           gp[0] = make_float2(g[0], g[1]);
           gp[1] = make_float2(g[2], g[3]);
           gp[2] = make_float2(g[4], g[5]);
@@ -1379,7 +1477,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
           kv[i + 2] = k4.z;
           kv[i + 3] = k4.w;
         }
-        const float *gk = Gk + (size_t)k * 6 * T;
+        const float *gk = Gk + (size_t)k * gst;
         if (nq == 6) {
           const float2 *g2 = reinterpret_cast<const float2 *>(gk);
           const float2 ga = g2[0], gb = g2[1], gc = g2[2];
@@ -1408,7 +1506,40 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
       for (int i = 0; i < R; i++)
 #pragma unroll
         for (int q = 0; q < 6; q++) acc[i][q] = 0.0f;
-    if (s.order == 2) {
+    if (MMA) {
+      // the whole CTA runs each pass on the tensor cores into Os (row j - 1 =
+      // rg R + i, column t NC + component), then each thread takes its block
+      if (s.order == 2) {
+        fp32_mma_contract<3, 3>(Ks, lay.kst, Gs, gst, Os, MT, kp8);
+        __syncthreads();
+        if (live)
+#pragma unroll
+          for (int i = 0; i < R; i++) {
+            const int j = j0 + i;
+#pragma unroll
+            for (int q = 0; q < 3; q++) acc[i][3 + q] = Os[(size_t)(j - 1) * gst + t * 3 + q];
+            if (j <= N)
+#pragma unroll
+              for (int q = 0; q < 3; q++) Gs[(size_t)j * gst + t * 6 + q] = w2f * acc[i][3 + q];
+          }
+        __syncthreads();  // the table's velocity rows hold the new deviations
+        fp32_mma_contract<3, 0>(Ks, lay.kst, Gs, gst, Os, MT, kp8);
+        __syncthreads();
+        if (live)
+#pragma unroll
+          for (int i = 0; i < R; i++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) acc[i][q] = Os[(size_t)(j0 + i - 1) * gst + t * 3 + q];
+      } else {
+        fp32_mma_contract<6, 0>(Ks, lay.kst, Gs, gst, Os, MT, kp8);
+        __syncthreads();
+        if (live)
+#pragma unroll
+          for (int i = 0; i < R; i++)
+#pragma unroll
+            for (int q = 0; q < 6; q++) acc[i][q] = Os[(size_t)(j0 + i - 1) * gst + t * 6 + q];
+      }
+    } else if (s.order == 2) {
       if (live) {
         contract(3, 3);
 #pragma unroll
@@ -1419,7 +1550,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
           // second-order FP64 sweep, whose residual already holds R_v)
           if (j <= N)
 #pragma unroll
-            for (int q = 0; q < 3; q++) Gs[((size_t)j * T + t) * 6 + q] = w2f * acc[i][3 + q];
+            for (int q = 0; q < 3; q++) Gs[(size_t)j * gst + t * 6 + q] = w2f * acc[i][3 + q];
         }
       }
       __syncthreads();  // the table's velocity rows hold the new deviations
@@ -1923,7 +2054,7 @@ size_t fp32_smem_bytes(const pc_plan *p) {
 // memory; failing both (N > 256) one trajectory per CTA.
 struct Fp32tShape {
   int R, RG, T, threads;
-  bool ksm, rsm, ok;
+  bool ksm, rsm, mma, ok;
   size_t smem;
 };
 constexpr size_t kMaxDynSmem = 220 * 1024;
@@ -1938,12 +2069,32 @@ Fp32tShape fp32t_shape(const pc_plan *p) {
     sh.RG = 4 * ((N + 31) / 32);
   }
   sh.ok = false;
-  if (p->tune.fp32_rows == 0 || sh.RG * 8 > kFp32tMaxThreads) return sh;
   const int want = std::max(8, std::min(p->tune.fp32_slots / 8 * 8, kFp32tMaxSlots));
+  if (p->opt.fp32_mma) {
+    // the tensor-core contraction: 4 rows per thread, node records from
+    // global memory, whatever fp32_rows says (the arithmetic is the option's,
+    // the launch shape the tuning's); FP32 multiply-adds only when N is too
+    // large for it
+    const int RG4 = 4 * ((N + 15) / 16);
+    int T = std::min(want, kFp32tMaxThreadsG / RG4 / 8 * 8);
+    while (T >= 8 && fp32t_smem_bytes(N, n, p->rows32, T, RG4, true, false, true, B) > kMaxDynSmem) T -= 8;
+    if (T >= 8) {
+      sh.R = 4;
+      sh.RG = RG4;
+      sh.T = T;
+      sh.ksm = sh.mma = true;
+      sh.rsm = false;
+      sh.ok = true;
+      sh.threads = sh.RG * sh.T;
+      sh.smem = fp32t_smem_bytes(N, n, p->rows32, T, RG4, true, false, true, B);
+      return sh;
+    }
+  }
+  if (p->tune.fp32_rows == 0 || sh.RG * 8 > kFp32tMaxThreads) return sh;
   // largest T <= want (multiple of 8) for a variant, 0 if none
   auto slots = [&](bool ksm, bool rsm) {
     int T = std::min(want, fp32t_max_threads(sh.R, rsm) / sh.RG / 8 * 8);
-    while (T >= 8 && fp32t_smem_bytes(n, p->rows32, T, sh.RG, ksm, rsm, B) > kMaxDynSmem) T -= 8;
+    while (T >= 8 && fp32t_smem_bytes(N, n, p->rows32, T, sh.RG, ksm, rsm, false, B) > kMaxDynSmem) T -= 8;
     return T >= 8 ? T : 0;
   };
   const int t_staged = slots(true, true);
@@ -1964,21 +2115,22 @@ Fp32tShape fp32t_shape(const pc_plan *p) {
   }
   sh.ok = true;
   sh.threads = sh.RG * sh.T;
-  sh.smem = fp32t_smem_bytes(n, p->rows32, sh.T, sh.RG, sh.ksm, sh.rsm, B);
+  sh.smem = fp32t_smem_bytes(N, n, p->rows32, sh.T, sh.RG, sh.ksm, sh.rsm, false, B);
   return sh;
 }
 
-template <int MODE, int R, bool KSM, bool RSM>
+template <int MODE, int R, bool KSM, bool RSM, bool MMA = false>
 void launch_fp32t_one(const pc_plan *p, const Fp32tShape &sh, const Sweep &s, const double *Yc, double *Yn,
                       const double *E, const float *R32, const Mix &mx, cudaStream_t st) {
   const Ctl &c = p->ws.ctl[p->ws.live];
-  k_fp32t<MODE, R, KSM, RSM><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), sh.threads, sh.smem, st>>>(
+  k_fp32t<MODE, R, KSM, RSM, MMA><<<sm_ctas(p, p->tune.fp32_ctas_per_sm), sh.threads, sh.smem, st>>>(
       s, c, p->model, p->d_K32R, p->rows32, p->d_mu32, Yc, Yn, E, R32, mx, sh.T);
 }
 
-template <int MODE, int R, bool KSM, bool RSM>
+template <int MODE, int R, bool KSM, bool RSM, bool MMA = false>
 cudaError_t fp32t_attr(size_t smem) {
-  return cudaFuncSetAttribute(k_fp32t<MODE, R, KSM, RSM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_fp32t<MODE, R, KSM, RSM, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
 }
 
 template <int MODE, int R>
@@ -1992,7 +2144,10 @@ void launch_fp32t_r(const pc_plan *p, const Fp32tShape &sh, const Sweep &s, cons
 template <int R>
 cudaError_t fp32t_attr_r(const Fp32tShape &sh) {
   cudaError_t e;
-  if (!sh.rsm) {
+  if (sh.mma) {
+    e = fp32t_attr<FP32_KEPLER, 4, true, false, true>(sh.smem);
+    if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, 4, true, false, true>(sh.smem);
+  } else if (!sh.rsm) {
     e = fp32t_attr<FP32_KEPLER, R, true, false>(sh.smem);
     if (e == cudaSuccess) e = fp32t_attr<FP32_CORR, R, true, false>(sh.smem);
   } else if (sh.ksm) {
@@ -2005,9 +2160,10 @@ cudaError_t fp32t_attr_r(const Fp32tShape &sh) {
   return e;
 }
 
-// FP32 sweeps of one mode over this round's list: the tiled kernel (T
-// trajectories per CTA), or with fp32_rows = 0 one trajectory per CTA of
-// 32 ceil((N+1)/32) threads.  Both give bitwise the same results.
+// FP32 sweeps of one mode over this round's list: with fp32_mma the tiled
+// kernel with its contraction on the tensor cores; otherwise the tiled kernel
+// (T trajectories per CTA) or, with fp32_rows = 0, one trajectory per CTA of
+// 32 ceil((N+1)/32) threads, which give bitwise the same results.
 template <int MODE>
 void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn, const double *E, const float *R32,
                  const Mix &mx, cudaStream_t st) {
@@ -2020,7 +2176,8 @@ void launch_fp32(const pc_plan *p, const Sweep &s, const double *Yc, double *Yn,
                                                                              Yc, Yn, E, R32, mx);
     return;
   }
-  if (sh.R == 4) launch_fp32t_r<MODE, 4>(p, sh, s, Yc, Yn, E, R32, mx, st);
+  if (sh.mma) launch_fp32t_one<MODE, 4, true, false, true>(p, sh, s, Yc, Yn, E, R32, mx, st);
+  else if (sh.R == 4) launch_fp32t_r<MODE, 4>(p, sh, s, Yc, Yn, E, R32, mx, st);
   else launch_fp32t_r<MODE, 8>(p, sh, s, Yc, Yn, E, R32, mx, st);
 }
 

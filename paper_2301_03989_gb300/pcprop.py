@@ -67,7 +67,7 @@ class Options(C.Structure):
                 ("warm_start", C.c_int), ("seg_mode", C.c_int), ("truncated", C.c_int), ("stall_sweeps", C.c_int),
                 ("stall_factor", C.c_double), ("div_limit", C.c_double), ("trunc_tol", C.c_double),
                 ("precision", C.c_int), ("switch_tol", C.c_double), ("max_rounds", C.c_longlong),
-                ("refine32", C.c_int), ("contraction", C.c_int), ("order", C.c_int)]
+                ("refine32", C.c_int), ("contraction", C.c_int), ("order", C.c_int), ("fp32_mma", C.c_int)]
 
 
 def lib():

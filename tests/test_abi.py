@@ -61,7 +61,7 @@ def test_argument_errors_without_a_gpu():
     o = pc.options_default(refine32=2)
     assert L.pc_plan_create(64, 4, C.byref(fm), None, C.byref(o), C.byref(out)) == E
     for bad_opts, N in ((dict(order=3), 64), (dict(order=2, contraction=pc.PC_CONTRACT_DMMA), 64),
-                        (dict(order=2), 300), (dict(contraction=2), 64)):
+                        (dict(order=2), 300), (dict(contraction=2), 64), (dict(fp32_mma=2), 64)):
         o = pc.options_default(**bad_opts)                                              # second order: split, N <= 255
         assert L.pc_plan_create(N, 4, C.byref(fm), None, C.byref(o), C.byref(out)) == E, bad_opts
     assert L.pc_propagate(null, 4, null, 0.0, 1.0, 0.0, null, null, null, null) == E

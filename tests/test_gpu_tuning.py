@@ -72,7 +72,8 @@ def test_fp32_variants_are_bitwise_neutral_on_few_bodies(pc):
     and the one-trajectory-per-CTA kernel give bitwise the same results."""
     import torch
     w = W.config3(M=600)
-    plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED, switch_tol=1e-6)
+    # FP32 multiply-adds (fp32_mma = 0): every tiled shape against the one-trajectory kernel
+    plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED, switch_tol=1e-6, fp32_mma=0)
     x0d = torch.as_tensor(W.to_planar(w.x0), device="cuda")
     tf = 0.3 * W.YEAR
     pc.set_tuning(plan, fp32_rows=0, fp32_ctas_per_sm=4)
