@@ -221,6 +221,21 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- our arm
+def fp32_mma_choice(args) -> int:
+    """pc_options.fp32_mma: the FP32 sweeps' contraction on the tensor cores
+    (three TF32 products) for the large synchronised batches (precision study,
+    uneven batch), FP32 multiply-adds with the autotuner's kernel choice for the
+    flyby workload's short lists with many bodies (one trajectory per CTA)."""
+    if args.fp32_mma != "auto":
+        return int(args.fp32_mma)
+    return 0 if args.workload == "flyby" else 1
+
+
+def fp32_contraction_note(args) -> str:
+    return ("tensor cores, three TF32 products (fp32_mma = 1)" if fp32_mma_choice(args)
+            else "FP32 multiply-adds (fp32_mma = 0)")
+
+
 def contract_flops_per_sweep(N: int) -> float:
     """Useful FP64 flops of one trajectory-sweep of the contraction: rows 1..N
     of K (row 0 is zero) times N+1 nodes times 6 components, 2 flops each."""
@@ -370,7 +385,8 @@ def run_ours(args, world, rank, local):
     t_plan = time.perf_counter()
     contraction = pc.PC_CONTRACT_SPLIT if args.contraction == "split" else pc.PC_CONTRACT_DMMA
     plan = pc.plan_from_workload(w, precision=pc.PC_PREC_MIXED if mixed else pc.PC_PREC_FP64,
-                                 switch_tol=switch_tol, contraction=contraction, order=args.order)
+                                 switch_tol=switch_tol, contraction=contraction, order=args.order,
+                                 fp32_mma=fp32_mma_choice(args))
     torch.cuda.synchronize(dev)
     plan_ms = 1000.0 * (time.perf_counter() - t_plan)   # operator build + uploads, reported apart
     stream = torch.cuda.Stream(device=dev)
@@ -513,6 +529,7 @@ def run_ours(args, world, rank, local):
                        "sweep_order": args.order,
                        "fp64_contraction": ("exact 8-bit digit products on the bf16 tensor cores"
                                             if args.contraction == "split" else "FP64 tensor cores (DMMA)"),
+                       "fp32_contraction": fp32_contraction_note(args) if mixed else None,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"dp{world}",
                        "tuning": tuning},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hx0.numel() * 8),
@@ -582,7 +599,7 @@ def run_aux(args, world, rank, local):
             prec = pc.PC_PREC_FP64 if args.precision == "fp64" else pc.PC_PREC_MIXED
             for d in degs:
                 o = pc.options_default(tol=b.tol, max_iters=b.max_iters, max_depth=b.max_depth, seg_mode=0,
-                                       precision=prec)
+                                       precision=prec, fp32_mma=fp32_mma_choice(args))
                 plans.append(pc.plan_create(int(d), 4, b.mu_central, b.mu, b.t_begin, b.granule, b.coef,
                                             b.indirect, o))
             x0 = torch.as_tensor(W.to_planar(uw.x0[perm]), device=dev)
@@ -606,7 +623,8 @@ def run_aux(args, world, rank, local):
             ms = float(np.mean(ms))
             metric = ("trajectories/s (uneven arcs 0.5-10 yr, N in {32,64,128,256}, 4-80 segments): "
                       + ("plain FP64" if args.precision == "fp64" else "mixed precision"))
-            config = {"workload": uw.name, "n_ic": M, "degrees": [int(d) for d in degs], "precision": args.precision}
+            config = {"workload": uw.name, "n_ic": M, "degrees": [int(d) for d in degs], "precision": args.precision,
+                      "fp32_contraction": fp32_contraction_note(args)}
         else:  # adjoint
             w = W.config4(M=args.n_ic or 1024)
             M = w.n_ic
@@ -669,6 +687,8 @@ def main(argv=None):
                          "stops falling)")
     ap.add_argument("--order", type=int, choices=[1, 2], default=2,
                     help="1: the paper's sweep; 2: its second-order form (both arms; the default)")
+    ap.add_argument("--fp32-mma", choices=["auto", "0", "1"], default="auto",
+                    help="FP32 sweeps' contraction on the tensor cores (auto: 1 except for the flyby workload)")
     ap.add_argument("--contraction", choices=["split", "dmma"], default="split",
                     help="FP64 contraction: exact digit products on the bf16 tensor cores, or the FP64 tensor cores")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")

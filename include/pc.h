@@ -140,14 +140,17 @@ typedef struct {
                           tensor cores as three TF32 products per term (K_hi G_lo + K_lo G_hi +
                           K_hi G_hi, each operand split into TF32 high and low parts; about 2^-22
                           per term, FP32 accumulation), 0 as FP32 multiply-adds.  Not in the
-                          paper.  Used by the tiled FP32 kernel when its trajectories' node
-                          records are read from global memory (4 rows per thread) */
+                          paper.  It fixes the FP32 kernel to the tiled shape with 4 rows per
+                          thread and node records read from global memory (launch tuning
+                          then varies only slots and CTAs per SM): faster on large
+                          synchronised batches with few bodies, slower on short lists with
+                          many bodies, where one trajectory per CTA wins */
 } pc_options;
 
 /* Fills *o with the defaults: tol 1e-13, relative 1, max_iters 60, max_depth 8,
  * warm_start 1, seg_mode 0, truncated 0, stall_sweeps 5, stall_factor 1e3,
  * div_limit 1e3, trunc_tol 1e-13, precision FP64, switch_tol 0, max_rounds 0, refine32 1,
- * contraction PC_CONTRACT_SPLIT, order 1, fp32_mma 1.
+ * contraction PC_CONTRACT_SPLIT, order 1, fp32_mma 0.
  * Returns PC_EINVAL if o is NULL. */
 pc_status pc_options_default(pc_options *o);
 

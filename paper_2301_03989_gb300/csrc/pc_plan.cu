@@ -88,7 +88,7 @@ extern "C" pc_status pc_options_default(pc_options *o) {
   o->refine32 = 1;
   o->contraction = PC_CONTRACT_SPLIT;
   o->order = 1;
-  o->fp32_mma = 1;
+  o->fp32_mma = 0;
   return PC_OK;
 }
 
