@@ -1404,7 +1404,12 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
   }
   __syncthreads();
 
-  const int j0 = rg * R + 1;  // first node of the thread's rows
+  // the thread's rows: R consecutive nodes from j0 (the multiply-add
+  // contraction loads them as float4s), or with the tensor-core contraction
+  // nodes 1 + rg + i RG, so that neighbouring lanes own neighbouring rows of
+  // the force and result tables (distinct banks) and node records
+  const int j0 = rg * R + 1;
+  auto row = [&](int i) { return MMA ? 1 + rg + i * RG : j0 + i; };
   const float *Kk = KSM ? Ks + rg * R : K32R + rg * R;
   const float *Gk = Gs + t * 6;
   int e = sl.e[t];
@@ -1449,7 +1454,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
       }
 #pragma unroll
       for (int i = 0; i < R; i++) {
-        const int j = j0 + i;
+        const int j = row(i);
         if (j <= N) {
           fp32_force_row<MODE>(rb + (size_t)j * rstr, B, mus, md.indirect, dl[i], w2f, g);
           float2 *gp = reinterpret_cast<float2 *>(Gs + (size_t)j * gst + t * 6);
@@ -1515,7 +1520,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
         if (live)
 #pragma unroll
           for (int i = 0; i < R; i++) {
-            const int j = j0 + i;
+            const int j = row(i);
 #pragma unroll
             for (int q = 0; q < 3; q++) acc[i][3 + q] = Os[(size_t)(j - 1) * gst + t * 3 + q];
             if (j <= N)
@@ -1529,7 +1534,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
 #pragma unroll
           for (int i = 0; i < R; i++)
 #pragma unroll
-            for (int q = 0; q < 3; q++) acc[i][q] = Os[(size_t)(j0 + i - 1) * gst + t * 3 + q];
+            for (int q = 0; q < 3; q++) acc[i][q] = Os[(size_t)(row(i) - 1) * gst + t * 3 + q];
       } else {
         fp32_mma_contract<6, 0>(Ks, lay.kst, Gs, gst, Os, MT, kp8);
         __syncthreads();
@@ -1537,14 +1542,14 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
 #pragma unroll
           for (int i = 0; i < R; i++)
 #pragma unroll
-            for (int q = 0; q < 6; q++) acc[i][q] = Os[(size_t)(j0 + i - 1) * gst + t * 6 + q];
+            for (int q = 0; q < 6; q++) acc[i][q] = Os[(size_t)(row(i) - 1) * gst + t * 6 + q];
       }
     } else if (s.order == 2) {
       if (live) {
         contract(3, 3);
 #pragma unroll
         for (int i = 0; i < R; i++) {
-          const int j = j0 + i;
+          const int j = row(i);
           // the position rows integrate the change of the sweep's velocities:
           // delta_v (new segment) or c_v - R_v (correction after a
           // second-order FP64 sweep, whose residual already holds R_v)
@@ -1562,7 +1567,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
       // change and size of the deviation, relative to the iterate
 #pragma unroll
       for (int i = 0; i < R; i++) {
-        const int j = j0 + i;
+        const int j = row(i);
         if (j <= N) {
           const float4 *rj = rb + (size_t)j * rstr;
           const float4 rk = rj[0], vk = rj[1];
@@ -1669,7 +1674,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
             for (int q = 0; q < 6; q++) Yn[(size_t)q * ld + m] = yk[q] + (double)0.0f;
 #pragma unroll
           for (int i = 0; i < R; i++) {
-            const int j = j0 + i;
+            const int j = row(i);
             if (j <= N)
 #pragma unroll
               for (int q = 0; q < 6; q++) Yn[((size_t)j * 6 + q) * ld + m] = yk[(size_t)j * 6 + q] + (double)dl[i][q];
@@ -1681,7 +1686,7 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
           for (int q = 0; q < 6; q++) Yn[(size_t)q * ld + m] = Yc[(size_t)q * ld + m] + (double)0.0f;
 #pragma unroll
         for (int i = 0; i < R; i++) {
-          const int j = j0 + i;
+          const int j = row(i);
           if (j <= N)
 #pragma unroll
             for (int q = 0; q < 6; q++) {
