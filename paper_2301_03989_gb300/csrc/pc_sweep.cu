@@ -616,8 +616,9 @@ constexpr int kTailVals = 14;
 constexpr int kForceNodes = 8;
 
 // Block = 32 FP64-list entries (x) by kForceNodes nodes (y); one thread per
-// (entry, node).
-__global__ void __launch_bounds__(32 * kForceNodes) k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y,
+// (entry, node).  Three blocks per SM (at most 80 registers): the kernel is
+// bound by GB300's FP64 pipe, and 16 warps per SM left it 68 % busy.
+__global__ void __launch_bounds__(32 * kForceNodes, 3) k_force(Sweep s, Ctl c, Model md, const double *__restrict__ Y,
                                                           const double *__restrict__ E,
                                                           const double *__restrict__ Aind, double *__restrict__ G,
                                                           const double *__restrict__ tau,
@@ -631,9 +632,8 @@ __global__ void __launch_bounds__(32 * kForceNodes) k_force(Sweep s, Ctl c, Mode
   const bool valid = i < count;
   const int m = valid ? s.l64[s.list_cur][i] : 0;
   const int ld = s.ld, N = s.N;
-  double acc[kTailVals];
-#pragma unroll
-  for (int v = 0; v < kTailVals; v++) acc[v] = 0.0;
+  // this node's resolution-sum terms go straight to shared memory (zero for
+  // an idle thread); thread ty = 0 adds the block's nodes in node order below
   if (valid && j <= N) {
     const double w2 = c.w2[m];
     const size_t yb = (size_t)j * 6 * ld + m;
@@ -656,16 +656,20 @@ __global__ void __launch_bounds__(32 * kForceNodes) k_force(Sweep s, Ctl c, Mode
     const double st = sg * tau[j];
 #pragma unroll
     for (int q = 0; q < 6; q++) {
-      acc[q] = sg * g[q];
-      acc[6 + q] = st * g[q];
+      red[ty][q][tx] = sg * g[q];
+      red[ty][6 + q][tx] = st * g[q];
     }
-    acc[12] = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-    acc[13] = y[3] * y[3] + y[4] * y[4] + y[5] * y[5];
-  }
+    red[ty][12][tx] = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    red[ty][13][tx] = y[3] * y[3] + y[4] * y[4] + y[5] * y[5];
+  } else {
 #pragma unroll
-  for (int v = 0; v < kTailVals; v++) red[ty][v][tx] = acc[v];
+    for (int v = 0; v < kTailVals; v++) red[ty][v][tx] = 0.0;
+  }
   __syncthreads();
   if (ty == 0 && valid) {
+    double acc[kTailVals];
+#pragma unroll
+    for (int v = 0; v < kTailVals; v++) acc[v] = red[0][v][tx];
     for (int u = 1; u < kForceNodes; u++) {
 #pragma unroll
       for (int v = 0; v < 12; v++) acc[v] += red[u][v][tx];
