@@ -55,9 +55,10 @@ IC_PER_RANK = {"precision": 65536, "flyby": 4096}
 # capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum over the
 # captured launches / their trajectory-sweeps); None until taken on the current
 # kernel.  A line's traffic is this figure times the launch's sweeps.
-# contract: k_contract_split on config 3 with 16,384 trajectories, 322 MB over
-# 7,460 trajectory-sweeps.
-TRAFFIC_BYTES_PER_SWEEP = {"contract": 43_200, "fp32": None}
+# (The last figure, 43.2 KB per trajectory-sweep for k_contract_split, was
+# taken on its first-order epilogue; both passes of the second-order sweep and
+# the FP32 convergence measure came after it.)
+TRAFFIC_BYTES_PER_SWEEP = {"contract": None, "fp32": None}
 
 
 def _peaks():
