@@ -107,8 +107,8 @@ struct Sweep {
   int order;                 // 1: the paper's sweep; 2: its second-order form
   int kep_stride;            // warm start solved at nodes 0, kep_stride, ..., N (0: at every node)
   const float *Lint;         // [2][n][17] interpolation weights (kep_stride > 0) as FP32 pairs hi + lo
-  float *YK17;               // [2][17][6][ld] Kepler solutions at those nodes minus the start state,
-                             // as FP32 pairs hi + lo
+  float *YK17;               // [17][6][ld] float2 (hi, lo): Kepler solutions at those nodes minus the
+                             // start state as FP32 pairs
   // Ephemeris of the round's new segments, evaluated once per distinct node-
   // time grid (w1, w2): an open-addressing table per round parity maps a grid
   // to its owning list entry and its index u in the cache EC.
@@ -174,7 +174,7 @@ struct Workspace {
   double *EX[2] = {nullptr, nullptr};   // [n][eih_stride(B)][ld] bodies' EIH data (c_light > 0; + repack target)
   // mixed precision (allocated when the plan asks for it), by new-segment list entry
   double *YK = nullptr;      // [entry][n][6] FP64 warm start
-  float *YK17 = nullptr;     // [2][17][6][ld] Kepler deviations at the interpolation nodes (FP32 pairs),
+  float *YK17 = nullptr;     // [17][6][ld] float2 Kepler deviations at the interpolation nodes (FP32 pairs),
                              // by new-segment entry
   // per-round ephemeris cache (model with bodies): tables by parity, per-entry
   // slots, grid owners and the cache itself

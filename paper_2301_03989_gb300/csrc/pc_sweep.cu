@@ -345,8 +345,8 @@ __global__ void k_kepler17(Sweep s, Ctl c, const double *__restrict__ tau) {
     for (int q = 0; q < 6; q++) {
       const double d = y[q] - x0[q];
       const float hi = ok ? (float)d : __int_as_float(0x7FC00000);
-      s.YK17[((size_t)k * 6 + q) * ld + e] = hi;
-      s.YK17[((size_t)(kKepNodes + k) * 6 + q) * ld + e] = ok ? (float)(d - (double)hi) : hi;
+      reinterpret_cast<float2 *>(s.YK17)[((size_t)k * 6 + q) * ld + e] =
+          make_float2(hi, ok ? (float)(d - (double)hi) : hi);
     }
   }
 }
@@ -507,8 +507,8 @@ __global__ void k_setup(Sweep s, Ctl c, Model md, const double *__restrict__ tau
           const float lh = Lh[k], ll = Ll[k];
 #pragma unroll
           for (int q = 0; q < 6; q++) {
-            const float dh = s.YK17[((size_t)k * 6 + q) * ld + e];
-            const float dl = s.YK17[((size_t)(kKepNodes + k) * 6 + q) * ld + e];
+            const float2 dd = reinterpret_cast<const float2 *>(s.YK17)[((size_t)k * 6 + q) * ld + e];
+            const float dh = dd.x, dl = dd.y;
             fin = fin && isfinite(dh);
             const float pr = __fmul_rn(lh, dh);
             const float pe = __fmaf_rn(lh, dh, -pr);  // lh dh - pr, exactly
