@@ -887,6 +887,11 @@ __global__ void __launch_bounds__(32 * kSplit) k_contract_diag(Sweep s, Ctl c, c
 // keeps Y' and allows no further corrections in this segment attempt.
 // ---------------------------------------------------------------------------
 constexpr float kFp32Floor = 2e-6f;
+// A correction solve stops at a change below 2e-5 of the correction: the FP64
+// sweep after it measures the change and decides convergence, so the floor
+// only trades FP32 sweeps against FP64 ones.  On config 3, 2e-5 cuts 8 % of the
+// FP32 sweeps with the same FP64 sweeps as 2e-6; 1e-4 adds 2 % FP64 sweeps.
+constexpr float kFp32CorrFloor = 2e-5f;
 constexpr int kFp32MaxThreads = 288;  // N + 1 <= 288
 
 // Shared-memory stride of a node record: an odd number of float4 so that the
@@ -1077,7 +1082,8 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
       }
       // The FP32 floor: the change cannot fall much below the rounding of the
       // contraction, ~sqrt(N) FP32 ulps of the deviation itself, so a change
-      // under kFp32Floor * max|deviation|/|y| ends the phase.  Failing to halve
+      // under kFp32Floor * max|deviation|/|y| ends the phase (a correction
+      // solve: kFp32CorrFloor times its correction).  Failing to halve
       // the best change for two sweeps (fluctuation at the floor) also ends it.
       if (emax < 0.5f * ebest) {
         nst = 0;
@@ -1085,7 +1091,8 @@ __global__ void __launch_bounds__(kFp32MaxThreads) k_fp32(Sweep s, Ctl c, Model 
         nst++;
       }
       ebest = fminf(ebest, emax);
-      if ((MODE == FP32_KEPLER && (double)emax < s.switch_tol) || emax < kFp32Floor * dmax || nst >= 2 ||
+      if ((MODE == FP32_KEPLER && (double)emax < s.switch_tol) ||
+          emax < (MODE == FP32_CORR ? kFp32CorrFloor : kFp32Floor) * dmax || nst >= 2 ||
           it >= s.max_iters)
         break;
       __syncthreads();  // the table is rewritten by the next sweep
@@ -1633,7 +1640,8 @@ __global__ void __launch_bounds__(fp32t_max_threads(R, RSM), 1)
         nst = (em < 0.5f * eb) ? 0 : nst + 1;
         sl.nst[tid] = nst;
         sl.ebest[tid] = fminf(eb, em);
-        if ((MODE == FP32_KEPLER && (double)em < s.switch_tol) || em < kFp32Floor * dm || nst >= 2 ||
+        if ((MODE == FP32_KEPLER && (double)em < s.switch_tol) ||
+            em < (MODE == FP32_CORR ? kFp32CorrFloor : kFp32Floor) * dm || nst >= 2 ||
             it >= s.max_iters)
           stop = 1;
       }
