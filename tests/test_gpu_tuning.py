@@ -133,6 +133,25 @@ def test_grid_cache_is_bitwise_neutral_on_shared_grids(pc, precision):
     plan.close()
 
 
+def test_grid_cache_over_capacity_is_bitwise_neutral(pc):
+    """40,000 flyby trajectories whose segments follow their own osculating
+    periods: every segment of the first round has its own node-time grid, more
+    than the cache's 32,768, so the grids past the capacity are evaluated per
+    segment; with the cache off all are.  Bitwise the same results."""
+    import torch
+    w = W.config2(M=40000)
+    x0d = torch.as_tensor(W.to_planar(w.x0), device="cuda")
+    tf = w.t0 + 2.0 * W.DAY
+    plan = pc.plan_from_workload(w)
+    base = _run(pc, plan, w, x0d, tf)
+    assert base[0] in (pc.PC_OK, pc.PC_ENOTCONV)
+    pc.set_tuning(plan, grid_cache=0)
+    r = _run(pc, plan, w, x0d, tf)
+    for a, b in zip(base[2:], r[2:]):
+        assert torch.equal(a, b)
+    plan.close()
+
+
 def test_tuning_validation(pc):
     w = W.config1(M=8)
     plan = pc.plan_from_workload(w)
