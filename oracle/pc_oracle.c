@@ -46,9 +46,10 @@
  *   ora_eih_terms        pinned: Schwarzschild closed form (one body at rest),
  *                                a body and a particle in uniform common motion
  *                                (the boosted rest-frame field), perihelion
- *                                advance 6 pi mu / (c^2 a (1 - e^2)); the terms
- *                                in the bodies' accelerations (1/2 d.A, 7/2 A/r)
- *                                are parity unpinned
+ *                                advance 6 pi mu / (c^2 a (1 - e^2)), and every
+ *                                term (those of the bodies' accelerations and
+ *                                potentials included) against the geodesic of
+ *                                the harmonic-gauge 1PN metric of the bodies
  *   order 2 of ora_pc_segment / ora_propagate
  *                        pinned: bitwise ora_pc2_segment on a segment; same
  *                                fixed point as order 1 end to end; Gauss-
