@@ -55,10 +55,10 @@ IC_PER_RANK = {"precision": 65536, "flyby": 4096}
 # capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum over the
 # captured launches / their trajectory-sweeps); None until taken on the current
 # kernel.  A line's traffic is this figure times the launch's sweeps.
-# (The last figure, 43.2 KB per trajectory-sweep for k_contract_split, was
-# taken on its first-order epilogue; both passes of the second-order sweep and
-# the FP32 convergence measure came after it.)
-TRAFFIC_BYTES_PER_SWEEP = {"contract": None, "fp32": None}
+# contract: k_contract_split, both passes of a second-order FP64 round with all
+# 16,384 trajectories of config 3 on the FP64 list (plain FP64 run, rounds 1
+# and 2): 334.5 and 331.8 MB per round, 20.3 KB per trajectory-sweep.
+TRAFFIC_BYTES_PER_SWEEP = {"contract": 20_300, "fp32": None}
 
 
 def _peaks():
@@ -325,13 +325,15 @@ def bf16_peak_tflops():
     return (v, "measured bf16 dense, sustained") if v else (1700.0, "fallback bf16 dense, sustained")
 
 
-def kernel_roofline(name, kt, steps, w, B, peaks, split=False):
+def kernel_roofline(name, kt, steps, w, B, peaks, split=False, order=2):
     """Roofline of one kernel from the instrumented replay: algorithmic flops of
     the trajectory-sweeps it ran / its summed launch time."""
     launches, ms = kt[name]
     extra = {}
     tb_key = name
     if name == "contract" and split and w.N <= 255:
+        if order != 2:
+            tb_key = None                   # the traffic figure is of the second-order passes
         sweeps = kt["sweeps64"]
         flops = split_flops_per_sweep(w.N) * sweeps
         peak, src = peaks["bf16_tensor"]
@@ -473,7 +475,8 @@ def run_ours(args, world, rank, local):
              "bf16_tensor": bf16_peak_tflops()}
     tsum = sum(ktimes[k][1] for k in names)
     kname = max(names, key=lambda k: ktimes[k][1])
-    by_kernel = {k: kernel_roofline(k, ktimes, args.prof_steps, w, nB, peaks, split=args.contraction == "split")
+    by_kernel = {k: kernel_roofline(k, ktimes, args.prof_steps, w, nB, peaks, split=args.contraction == "split",
+                                    order=args.order)
                  for k in ("contract", "fp32")}
     roof = by_kernel.get(kname) or by_kernel["contract"]
     roof = dict(roof, dominant_by_time=kname,
